@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark: Gcell-steps/s of the swept-rule solver against the Standard
+solver on one B300 (FP64), with the roofline of its dominant kernel.
+
+One bench step = one whole run of the workload: the isentropic vortex on a
+256 x 256 periodic grid (beta = 5, rho = p = 1, u = v = 1, gamma = 1.4, CFL
+0.25) advanced to t = 10, i.e. 2999 RK2 steps, swept block 32, depth 6
+(6 stage-levels per phase).  Inputs are seeded and synthetic and stay
+resident in device memory; L2 is flushed (a 256 MiB write) between timed
+iterations.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload euler256|heat64|heat16384]
+
+--impl reference times the CPU oracle (the plain fp64 C reference) on the
+host cores on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs its own replica; the solver has no data-path
+exchange on one GPU.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-steps/s Swept vs Standard (FP64, 1 B300); % of HBM roofline"
+UNIT = "Gcell-steps/s"
+
+# Algorithmic FP64 work per cell and stage of the arithmetic specification
+# (fma = 2 flops; add, mul, div, sqrt = 1): heat 3 adds + 2 fma = 7; Euler 187
+# (cell pressure 9, limiter 6, two faces of 76, update 20).
+FLOPS_PER_CELL_STAGE = {"heat": 7, "euler": 187}
+# FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA lanes per clock
+# (measured: 565 G FMA/s at 1.94 GHz) x 2 flops x 2032 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload(name):
+    from paper_2105_10332_b300 import workloads as W
+    if name == "euler256":
+        q0, dx = W.vortex(256)
+        dt, N = W.vortex_dt(q0, dx, 10.0, cfl=0.25)
+        return dict(name="euler_vortex_256x256_t10", eqn="euler", nx=256, ny=256, dt=dt, dx=dx,
+                    nsteps=N, tile=32, depth=6, state=q0)
+    if name == "heat64":
+        dt, dx = W.heat_dt(64, 0.1)
+        return dict(name="heat_sine_64x64_500steps", eqn="heat", nx=64, ny=64, dt=dt, dx=dx,
+                    nsteps=500, tile=16, depth=6, state=W.heat_sine(64, 64))
+    if name == "heat16384":
+        dt, dx = W.heat_dt(16384, 0.1)
+        return dict(name="heat_modes_16384x16384_2000steps", eqn="heat", nx=16384, ny=16384,
+                    dt=dt, dx=dx, nsteps=2000, tile=32, depth=14,
+                    state=W.heat_modes(16384, 16384))
+    raise SystemExit("unknown workload %s" % name)
+
+
+def shape_cells(eqn, b, d, kind, tiles):
+    """Algorithmic cell-stages one launch of a swept kernel computes."""
+    n = 1 if eqn == "heat" else 2
+    up = sum((b - 2 * s * n) ** 2 for s in range(1, d + 1))
+    lower = sum((2 * s * n) ** 2 for s in range(1, d + 1))
+    bridge = 2 * sum((2 * s * n) * (b - 2 * s * n) for s in range(1, d + 1))
+    return tiles * {"up_pyramid": up, "bridges": bridge, "octahedron": lower + up,
+                    "down_pyramid": lower}[kind]
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(wl, budget_s):
+    """Time the CPU oracle on whole chunks of the workload until budget_s passes.
+    Returns (Gcell-steps/s, steps run, seconds)."""
+    import oracle
+    cells = wl["nx"] * wl["ny"]
+    state = wl["state"]
+    steps, t_total = 0, 0.0
+    chunk = max(1, int(2e7 // (cells * (40 if wl["eqn"] == "euler" else 1))))
+    while t_total < budget_s and steps < wl["nsteps"]:
+        c = min(chunk, wl["nsteps"] - steps)
+        t0 = time.perf_counter()
+        if wl["eqn"] == "euler":
+            state = oracle.euler_run(state, wl["dt"], wl["dx"], c)
+        else:
+            state = oracle.heat_run(state, (wl["dt"]) / (wl["dx"] * wl["dx"]), c)
+        t_total += time.perf_counter() - t0
+        steps += c
+    return cells * steps / t_total / 1e9, steps, t_total
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    for _ in range(args.warmup):
+        oracle_sample(wl, 0.5)
+    vals, secs, nsteps = [], 0.0, 0
+    for _ in range(args.steps):
+        v, n, s = oracle_sample(wl, 5.0)
+        vals.append(v)
+        secs += s
+        nsteps += n
+    value = wl["nx"] * wl["ny"] * nsteps / secs / 1e9
+    sample = ("%d RK2 steps per bench step of the %s workload (first steps of the run), "
+              "oracle compiled -O2 -ffp-contract=off, OpenMP" % (nsteps // args.steps, wl["name"]))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * secs / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "nx": wl["nx"], "ny": wl["ny"],
+                       "steps_per_run": wl["nsteps"], "solver": "cpu oracle, step by step"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+    from paper_2105_10332_b300 import sweep as S
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"])
+    N, cells = wl["nsteps"], wl["nx"] * wl["ny"]
+    init = torch.from_numpy(wl["state"]).to(dev)
+    state = init.clone()
+    ws = solver.workspace(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(method, K):
+        evs = []
+        for _ in range(K):
+            state.copy_(init)
+            flush.fill_(1)  # evict the state and level store from L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            getattr(solver, method)(state, N, ws)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        solver.run_swept(state, N, ws)
+        solver.run_standard(state, N, ws)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K swept runs
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with sampler:
+        ms_swept = timed("run_swept", args.steps)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms_swept = max_over_ranks(ms_swept)
+    clocks = sampler.summary()
+
+    # the Standard solver on the same workload, same protocol
+    barrier()
+    torch.cuda.synchronize(dev)
+    ms_std = max_over_ranks(timed("run_standard", args.steps))
+    barrier()
+
+    # per-kernel durations: one more swept run with an event pair around each launch
+    solver.set("profile", 1)
+    state.copy_(init)
+    flush.fill_(1)
+    solver.run_swept(state, N, ws)
+    prof = solver.profile()
+    solver.set("profile", 0)
+    launches_per_run = sum(n for _, n in prof.values())
+
+    # end to end through the public API with host buffers (pinned): H2D copy,
+    # run, D2H copy inside the timed region
+    host0 = torch.from_numpy(wl["state"]).pin_memory()
+    host = host0.clone().pin_memory()
+    K_e2e = max(1, min(args.steps, 3))
+    e2e_s = 0.0
+    for _ in range(K_e2e):
+        host.copy_(host0)
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        solver.run_swept(host, N)
+        torch.cuda.synchronize(dev)
+        e2e_s += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s)
+    state_bytes = init.numel() * 8
+
+    value = world * cells * N * args.steps / (ms_swept / 1e3) / 1e9
+    v_std = world * cells * N * args.steps / (ms_std / 1e3) / 1e9
+    v_e2e = world * cells * N * K_e2e / e2e_s / 1e9
+
+    # roofline of the dominant kernel (FP64 ALU bound)
+    tiles = (wl["nx"] // wl["tile"]) * (wl["ny"] // wl["tile"])
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    if dom == "standard":
+        dom_cells = 2 * cells
+    else:
+        dom_cells = shape_cells(wl["eqn"], wl["tile"], wl["depth"], dom, tiles)
+    flops = dom_cells * FLOPS_PER_CELL_STAGE[wl["eqn"]]
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "kernel": dom, "launch_ms": round(dom_ms, 5),
+                "flops_per_launch": flops, "peak_basis": "FP64 148 SMs x 2 FMA/clk x 2032 MHz (derived)",
+                "kernels": {k: {"ms_total": round(v[0], 4), "launches": v[1]} for k, v in prof.items()}}
+
+    line = None
+    if rank == 0:
+        os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+        cb_value, cb_steps, cb_secs = oracle_sample(wl, 12.0)
+        cpu_baseline = {"value": round(cb_value, 6), "unit": UNIT,
+                        "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+                        "sample": "first %d of %d RK2 steps of the same workload, %.1f s"
+                                  % (cb_steps, N, cb_secs)}
+        line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms_swept / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded isentropic vortex / heat modes)",
+                "config": {"workload": wl["name"], "nx": wl["nx"], "ny": wl["ny"],
+                           "steps_per_run": N, "tile": wl["tile"], "depth": wl["depth"],
+                           "standard_tile": int(solver.get("standard_tile")),
+                           "l2": "flushed (256 MiB write) between timed iterations",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "standard": {"value": round(v_std, 6), "ms_per_step": round(ms_std / args.steps, 3)},
+                "swept_over_standard": round(value / v_std, 4),
+                "e2e": {"value": round(v_e2e, 6), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes},
+                "gpu_launches": int(launches_per_run * args.steps),
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="euler256")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * sweep.h -- C ABI of the B300 swept-rule solver for explicit 2D stencil PDEs.
+ *
+ * The solver advances a periodic 2D field with the two-dimensional swept
+ * rule (Walker & Niemeyer, Sec. 3.3): each block of the grid is taken through
+ * Up-Pyramid, X/Y-Bridge, Octahedron and Down-Pyramid phases, advancing as
+ * many RK stages on chip as its dependency cone allows before its edges go
+ * back to device memory.  A conventional one-kernel-per-step solver
+ * ("Standard", Sec. 3.1) gives the same result bit for bit.
+ *
+ * Equations (time rule: explicit midpoint RK2 unless set otherwise):
+ *   SWEEP_HEAT  -- T_t = alpha (T_xx + T_yy), 5-point Laplacian (App. A).
+ *                  State: 1 component.  Stencil radius per stage n = 1.
+ *   SWEEP_EULER -- compressible Euler, ideal gas (App. B): pressure-ratio
+ *                  minmod reconstruction, Rusanov-form flux.
+ *                  State: 4 components (rho, rho u, rho v, E).  n = 2.
+ *
+ * Conventions shared by every entry point:
+ *   - All arithmetic is IEEE binary64.
+ *   - State layout: structure of arrays [ncomp][ny][nx], x fastest,
+ *     contiguous, base address 16-byte aligned.  Periodic in x and y.
+ *     Cell (i, j) of the heat problem sits at x = i dx, y = j dx; the Euler
+ *     problem stores cell averages.  dy = dx.
+ *   - Ownership: the state and the workspace are device memory owned by the
+ *     caller (e.g. torch tensors).  The handle owns host-side tables only.
+ *     No entry point allocates device memory.
+ *   - Streams: work is enqueued on the given stream (a cudaStream_t; NULL
+ *     is the legacy default stream) and the call returns without waiting,
+ *     like a CUDA library call.  Launch-configuration errors are reported by
+ *     the return code; a fault during execution surfaces at the caller's
+ *     next synchronisation.  No entry point synchronises the device unless
+ *     its comment says so, so the enqueued sequence can be captured into a
+ *     CUDA graph.
+ *   - Errors: a nonzero sweep_status; nothing aborts, exits or traps.
+ *   - Threads: one handle must not be used from two threads at once;
+ *     separate handles are independent.
+ */
+#ifndef SWEEP_H
+#define SWEEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* the type behind cudaStream_t */
+
+typedef struct sweep_s sweep_t; /* opaque solver handle */
+
+enum sweep_eqn { SWEEP_HEAT = 0, SWEEP_EULER = 1 };
+
+enum sweep_status {
+    SWEEP_OK = 0,
+    SWEEP_EINVAL = 1,      /* bad argument or geometry                       */
+    SWEEP_ENOMEM = 2,      /* host allocation failed                         */
+    SWEEP_ECUDA = 3,       /* a CUDA call or kernel launch failed            */
+    SWEEP_ETIMEOUT = 4,    /* a bounded device-side wait gave up             */
+    SWEEP_EUNSUPPORTED = 5 /* valid request that this build does not handle  */
+};
+
+/*
+ * Create a solver for an nx x ny periodic grid.
+ *   eqn    SWEEP_HEAT or SWEEP_EULER.
+ *   dt, dx time step and cell size (dy = dx); heat uses r = alpha dt / dx^2.
+ *   tile   block edge b of the swept decomposition (Sec. 3.2): even,
+ *          b > 2n, nx % b == 0, ny % b == 0, nx/b >= 2, ny/b >= 2.
+ *   depth  stage-levels per swept phase d: 2 <= d <= k = b/(2n) - 1 (Eq. 1),
+ *          d even so that every phase ends on a whole RK2 step; 0 picks the
+ *          largest even d allowed.
+ * Defaults: alpha = 1, gamma = 1.4, limiter 0, RK2.  The Standard solver
+ * uses its own block edge ("standard_tile", default 32 for heat, 16 for
+ * Euler).  On success *out receives the handle (destroy with
+ * sweep_destroy).  Returns SWEEP_EINVAL for any violated bound.
+ */
+int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile, int depth,
+                 sweep_t **out);
+
+/*
+ * Set a scalar parameter.  Keys:
+ *   "alpha"          heat diffusivity (> 0)
+ *   "gamma"          ratio of specific heats (> 1)
+ *   "limiter"        0 pressure-ratio minmod, textbook orientation (App. B,
+ *                    reading of the garbled ratio); 1 the orientation as printed
+ *   "scheme"         heat time rule: 0 RK2 midpoint, 1 forward Euler (App. A)
+ *   "standard_tile"  block edge of the Standard solver (8..64, divides nx, ny)
+ *   "profile"        1: every later run brackets each kernel launch with a
+ *                    pair of CUDA events on its stream (read them with
+ *                    sweep_profile_read); 0 (default): no events
+ * Returns SWEEP_EINVAL for an unknown key or a value out of range.
+ */
+int sweep_set_param(sweep_t *h, const char *key, double value);
+
+/* Read back a parameter (the keys above plus "tile", "depth", "r",
+ * "nx", "ny", "ncomp", "radius").  Returns SWEEP_EINVAL for an unknown key. */
+int sweep_get_param(const sweep_t *h, const char *key, double *value);
+
+/*
+ * Bytes of device workspace that sweep_run_swept and sweep_run_standard need
+ * (256-byte aligned base): (depth + 1) level slots of one state each plus a
+ * small header.  The Standard solver needs only the first slot.
+ */
+size_t sweep_workspace_bytes(const sweep_t *h);
+
+/*
+ * Advance d_state (device, [ncomp][ny][nx] fp64) in place by exactly nsteps
+ * time steps with the swept rule (Sec. 3.3): Up-Pyramid, then
+ * [Bridges, Octahedron] cycles with the block grid shifted by b/2 each
+ * cycle, then Bridges and Down-Pyramid; the 2*nsteps mod depth stage-levels
+ * that do not fill a cycle are taken as Standard steps.  Bit-identical to
+ * sweep_run_standard.  d_ws: caller-owned device workspace of
+ * sweep_workspace_bytes(h) bytes, 256-byte aligned; its contents on entry
+ * do not matter.  nsteps >= 0.
+ */
+int sweep_run_swept(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
+                    struct CUstream_st *stream);
+
+/*
+ * Advance d_state in place by nsteps with the Standard solver (Sec. 3.1):
+ * one kernel per RK2 step, each block loading its tile plus a 2n halo,
+ * taking stage 1 on the tile plus an n halo and stage 2 on the tile.
+ */
+int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
+                       struct CUstream_st *stream);
+
+/*
+ * Per-kernel device time of the launches recorded since "profile" was set
+ * or since the last read.  Kinds: 0 Up-Pyramid, 1 Bridges, 2 Octahedron,
+ * 3 Down-Pyramid, 4 Standard step.  ms[k] receives the summed event time of
+ * kind k and launches[k] the number of its launches, for k < nkinds.  Waits
+ * for the recorded events (synchronises with the stream they were recorded
+ * on).  Returns SWEEP_ECUDA if an event cannot be read.
+ */
+int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds);
+
+/* Release a handle (NULL is ignored). */
+void sweep_destroy(sweep_t *h);
+
+/* Static description of a status code. */
+const char *sweep_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEEP_H */

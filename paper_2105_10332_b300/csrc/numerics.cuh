@@ -1,0 +1,139 @@
+// numerics.cuh -- pointwise stage updates of the two problems, FP64.
+//
+// Every operation is an explicit round-to-nearest intrinsic (__dadd_rn,
+// __dmul_rn, __fma_rn, __ddiv_rn, __dsqrt_rn) so that the compiler cannot
+// fuse or reorder anything; the library is also built with -fmad=false.
+// The rounding order is the one the method's arithmetic specification pins
+// (the paper gives none), so that the Swept and Standard kernels -- which
+// both call these functions -- agree bit for bit, and agree with any other
+// implementation of the same specification.
+#pragma once
+
+#include <cstdint>
+
+namespace sweep {
+
+// ---------------------------------------------------------------- heat, App. A
+// t = fma(-4, T, (T_W + T_E) + (T_S + T_N));  T' = fma(c, t, T_own)
+// with c = r/2 for the first RK2 stage and r for the second (App. A update
+// with r_x = r_y = r, taken as a midpoint rule).
+__device__ __forceinline__ double heat_update(double uc, double uw, double ue, double us,
+                                              double un, double own, double c)
+{
+    const double s = __dadd_rn(__dadd_rn(uw, ue), __dadd_rn(us, un));
+    const double t = __fma_rn(-4.0, uc, s);
+    return __fma_rn(c, t, own);
+}
+
+// ---------------------------------------------------------------- Euler, App. B
+struct EulerConst {
+    double gamma;  // ratio of specific heats
+    double gm1;    // gamma - 1 (rounded once, on the host)
+};
+
+// Cell pressure for the limiter, symmetric in x and y:
+// inv = 1/rho, u = m_x inv, v = m_y inv, p = (gamma-1) fma(-1/2, m_x u + m_y v, E)
+__device__ __forceinline__ double cell_pressure(double rho, double mx, double my, double E,
+                                                const EulerConst &k)
+{
+    const double inv = __ddiv_rn(1.0, rho);
+    const double u = __dmul_rn(mx, inv);
+    const double v = __dmul_rn(my, inv);
+    const double ke2 = __dadd_rn(__dmul_rn(mx, u), __dmul_rn(my, v));
+    return __dmul_rn(k.gm1, __fma_rn(-0.5, ke2, E));
+}
+
+// Half limiter factors of one cell along one axis from dm = P_i - P_{i-1} and
+// dp = P_{i+1} - P_i: hp = phi_plus/2 (towards the + face), hm = phi_minus/2.
+// phi_plus = min(dm/dp, 1), phi_minus = min(dp/dm, 1) where both differences
+// are nonzero with equal signs, else 0 (pressure-ratio minmod, App. B).
+// One division suffices: when |dm| < |dp| the exact dm/dp is below 1, so its
+// rounding is <= 1 and min() keeps it, while dp/dm > 1 rounds to >= 1 and
+// min() gives 1; symmetrically otherwise.  The sign and magnitude tests are
+// integer operations on the bit patterns, which keeps them off the FP64 pipe.
+// literal != 0 swaps the two factors (the orientation printed in App. B).
+__device__ __forceinline__ void limiter_halves(double dm, double dp, int literal, double &hp,
+                                               double &hm)
+{
+    const unsigned long long bm = (unsigned long long)__double_as_longlong(dm);
+    const unsigned long long bp = (unsigned long long)__double_as_longlong(dp);
+    const unsigned long long am = bm & 0x7fffffffffffffffull;
+    const unsigned long long ap = bp & 0x7fffffffffffffffull;
+    const bool same = ((bm ^ bp) >> 63) == 0 && am != 0 && ap != 0;
+    const bool mlt = am < ap;  // |dm| < |dp|
+    const double q = __ddiv_rn(mlt ? dm : dp, mlt ? dp : dm);
+    const double hq = __dmul_rn(0.5, q);
+    double plus = mlt ? hq : 0.5;
+    double minus = mlt ? 0.5 : hq;
+    if (!same) {
+        plus = 0.0;
+        minus = 0.0;
+    }
+    if (literal) {
+        hp = minus;
+        hm = plus;
+    } else {
+        hp = plus;
+        hm = minus;
+    }
+}
+
+// Flux of one reconstructed state in the face-normal frame (rho, m_n, m_t, E):
+// inv = 1/rho, u_n = m_n inv, u_t = m_t inv,
+// p = (gamma-1) fma(-1/2, fma(m_n, u_n, m_t u_t), E), c = sqrt((gamma p) inv),
+// f = (m_n, fma(m_n, u_n, p), m_t u_n, (E + p) u_n), lam = |u_n| + c.
+__device__ __forceinline__ void state_flux(double rho, double mn, double mt, double E,
+                                           const EulerConst &k, double f[4], double &lam)
+{
+    const double inv = __ddiv_rn(1.0, rho);
+    const double un = __dmul_rn(mn, inv);
+    const double ut = __dmul_rn(mt, inv);
+    const double ke2 = __fma_rn(mn, un, __dmul_rn(mt, ut));
+    const double p = __dmul_rn(k.gm1, __fma_rn(-0.5, ke2, E));
+    const double c = __dsqrt_rn(__dmul_rn(__dmul_rn(k.gamma, p), inv));
+    f[0] = mn;
+    f[1] = __fma_rn(mn, un, p);
+    f[2] = __dmul_rn(mt, un);
+    f[3] = __dmul_rn(__dadd_rn(E, p), un);
+    lam = __dadd_rn(fabs(un), c);
+}
+
+// larger of two non-negative, non-NaN doubles by their bit patterns (integer
+// compare, same result as the floating-point max for such values)
+__device__ __forceinline__ double max_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+
+// Rusanov-form numerical flux (App. B) at the face between cells "0" and "1",
+// states in the face-normal frame, hl = phi_plus(0)/2, hr = phi_minus(1)/2:
+//   Q_L = fma(hl, Q1 - Q0, Q0),  Q_R = fma(-hr, Q1 - Q0, Q1)
+//   Fh = 1/2 fma(r, Q_L - Q_R, F(Q_L) + F(Q_R)),  r = max(lam_L, lam_R)
+__device__ __forceinline__ void face_flux(const double q0[4], const double q1[4], double hl,
+                                          double hr, const EulerConst &k, double fh[4])
+{
+    double ql[4], qr[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double dq = __dadd_rn(q1[c], -q0[c]);
+        ql[c] = __fma_rn(hl, dq, q0[c]);
+        qr[c] = __fma_rn(-hr, dq, q1[c]);
+    }
+    double fl[4], fr[4], laml, lamr;
+    state_flux(ql[0], ql[1], ql[2], ql[3], k, fl, laml);
+    state_flux(qr[0], qr[1], qr[2], qr[3], k, fr, lamr);
+    const double r = max_nonneg(laml, lamr);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        fh[c] = __dmul_rn(0.5, __fma_rn(r, __dadd_rn(ql[c], -qr[c]), __dadd_rn(fl[c], fr[c])));
+}
+
+// out = fma(lam, (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2} - Gh_{j+1/2}), own)
+__device__ __forceinline__ double euler_combine(double fm, double fp, double gm, double gp,
+                                                double own, double lam)
+{
+    const double d = __dadd_rn(__dadd_rn(fm, -fp), __dadd_rn(gm, -gp));
+    return __fma_rn(lam, d, own);
+}
+
+}  // namespace sweep

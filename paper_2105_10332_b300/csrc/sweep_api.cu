@@ -1,0 +1,370 @@
+// sweep_api.cu -- the C ABI of include/sweep.h: handle, argument checks,
+// workspace sizing and the launch sequences of the Swept and Standard solvers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "sweep.h"
+
+using namespace sweep;
+
+struct sweep_s {
+    int eqn;
+    int64_t nx, ny;
+    double dt, dx;
+    int tile, depth;
+    double alpha, gamma;
+    int limiter;   // 0 textbook orientation, 1 as printed
+    int scheme;    // heat: 0 RK2 midpoint, 1 forward Euler
+    int std_tile;
+    // optional per-launch event timing ("profile" parameter)
+    int profile;
+    std::vector<cudaEvent_t> ev;   // start/end pairs, reused across runs
+    std::vector<int> ev_kind;      // kernel kind of each recorded pair
+    size_t ev_used;                // pairs recorded since the last read
+};
+
+namespace {
+
+constexpr size_t kHeader = 256;
+
+int radius(int eqn) { return eqn == SWEEP_HEAT ? 1 : 2; }
+int ncomp(int eqn) { return eqn == SWEEP_HEAT ? 1 : 4; }
+
+int64_t slot_elems(const sweep_s *h)
+{
+    const int64_t e = (int64_t)ncomp(h->eqn) * h->nx * h->ny;
+    return (e + 31) / 32 * 32;  // 256-byte multiple
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// largest shared-memory window the kernels accept
+int max_window(int eqn)
+{
+    int w = 8;
+    while (true) {
+        const size_t s = eqn == SWEEP_HEAT ? smem_bytes<Heat>(w + 2) : smem_bytes<Euler>(w + 2);
+        if (s > 227 * 1024) return w;
+        w += 2;
+    }
+}
+
+bool valid_std_tile(const sweep_s *h, int t)
+{
+    const int n = radius(h->eqn);
+    if (t < 8 || t > 64 || h->nx % t != 0 || h->ny % t != 0) return false;
+    return t + 4 * n <= max_window(h->eqn);
+}
+
+Params make_params(const sweep_s *h, double *state, void *ws)
+{
+    Params p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.b = h->tile;
+    p.d = h->depth;
+    p.tiles_x = (int)(h->nx / h->tile);
+    p.tiles_y = (int)(h->ny / h->tile);
+    p.std_tile = h->std_tile;
+    if (h->eqn == SWEEP_HEAT) {
+        const double r = (h->alpha * h->dt) / (h->dx * h->dx);
+        p.c1 = 0.5 * r;
+        p.c2 = r;
+    } else {
+        const double lam = h->dt / h->dx;
+        p.c1 = 0.5 * lam;
+        p.c2 = lam;
+    }
+    p.ek.gamma = h->gamma;
+    p.ek.gm1 = h->gamma - 1.0;
+    p.literal = h->limiter;
+    p.state = state;
+    p.ws = ws ? (double *)((char *)ws + kHeader) : nullptr;
+    p.slot_elems = slot_elems(h);
+    return p;
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Kernel kinds for the profile counters.
+enum { kKindUp = 0, kKindBridges = 1, kKindOctahedron = 2, kKindDown = 3, kKindStandard = 4,
+       kKinds = 5 };
+
+// Event bracket around one launch when profiling is on.
+struct Bracket {
+    sweep_s *h;
+    cudaStream_t st;
+    size_t i;
+    bool on;
+    Bracket(const sweep_s *hc, cudaStream_t s, int kind) : h(const_cast<sweep_s *>(hc)), st(s), i(0), on(false)
+    {
+        if (!h->profile) return;
+        i = h->ev_used;
+        if (2 * (i + 1) > h->ev.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) {
+                cudaEventDestroy(a);
+                return;
+            }
+            h->ev.push_back(a);
+            h->ev.push_back(b);
+            h->ev_kind.push_back(kind);
+        }
+        h->ev_kind[i] = kind;
+        on = cudaEventRecord(h->ev[2 * i], st) == cudaSuccess;
+    }
+    ~Bracket()
+    {
+        if (on && cudaEventRecord(h->ev[2 * i + 1], st) == cudaSuccess) h->ev_used = i + 1;
+    }
+};
+
+// Standard steps: ping-pong between the state and slot 0 of the workspace,
+// ending in the state.
+template <class EQ>
+int standard_steps(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    if (nsteps <= 0) return SWEEP_OK;
+    const int T = h->std_tile;
+    const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N);
+    if (set_smem(k_standard<EQ>, smem) != cudaSuccess) return SWEEP_ECUDA;
+    const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
+    double *a = p.state, *b = p.ws;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        {
+            Bracket br(h, st, kKindStandard);
+            k_standard<EQ><<<grid, kThreads, smem, st>>>(p, a, b);
+        }
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
+    if (a != p.state) {
+        const size_t bytes = sizeof(double) * (size_t)ncomp(h->eqn) * h->nx * h->ny;
+        if (cudaMemcpyAsync(p.state, a, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return SWEEP_ECUDA;
+    }
+    return SWEEP_OK;
+}
+
+template <class EQ>
+int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    const int64_t L = 2 * nsteps;
+    const int d = h->depth;
+    int64_t done = 0;
+    if (L >= d) {
+        const size_t smem = smem_bytes<EQ>(h->tile);
+        if (set_smem(k_up<EQ>, smem) != cudaSuccess || set_smem(k_bridges<EQ>, smem) != cudaSuccess ||
+            set_smem(k_octahedron<EQ>, smem) != cudaSuccess)
+            return SWEEP_ECUDA;
+        const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
+        const int64_t m = L / d - 1;  // whole [Bridges, Octahedron] cycles
+        {
+            Bracket br(h, st, kKindUp);
+            k_up<EQ><<<tiles, kThreads, smem, st>>>(p);
+        }
+        for (int64_t c = 0; c <= m; ++c) {
+            const int o = (c & 1) ? h->tile / 2 : 0;
+            const int64_t base = c * d;
+            {
+                Bracket br(h, st, kKindBridges);
+                k_bridges<EQ><<<2 * tiles, kThreads, smem, st>>>(p, base, o);
+            }
+            {
+                Bracket br(h, st, c == m ? kKindDown : kKindOctahedron);
+                k_octahedron<EQ><<<tiles, kThreads, smem, st>>>(p, base, o, c == m ? 1 : 0);
+            }
+        }
+        if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
+        done = (m + 1) * d;
+    }
+    return standard_steps<EQ>(h, p, (L - done) / 2, st);
+}
+
+int check_run(const sweep_t *h, const double *state, int64_t nsteps, const void *ws)
+{
+    if (!h || !state || !ws || nsteps < 0) return SWEEP_EINVAL;
+    if (!aligned(state, 16) || !aligned(ws, 256)) return SWEEP_EINVAL;
+    if (h->eqn == SWEEP_HEAT && h->scheme != 0) return SWEEP_EUNSUPPORTED;
+    return SWEEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+#define SWEEP_API __attribute__((visibility("default")))
+
+SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile, int depth,
+                 sweep_t **out)
+{
+    if (!out) return SWEEP_EINVAL;
+    *out = nullptr;
+    if (eqn != SWEEP_HEAT && eqn != SWEEP_EULER) return SWEEP_EINVAL;
+    if (!(std::isfinite(dt) && dt > 0.0 && std::isfinite(dx) && dx > 0.0)) return SWEEP_EINVAL;
+    const int n = radius(eqn);
+    if (tile <= 2 * n || (tile % 2) != 0 || tile > max_window(eqn)) return SWEEP_EINVAL;
+    if (nx <= 0 || ny <= 0 || nx % tile != 0 || ny % tile != 0) return SWEEP_EINVAL;
+    if (nx / tile < 2 || ny / tile < 2) return SWEEP_EINVAL;
+    if (nx > (int64_t(1) << 31) || ny > (int64_t(1) << 31)) return SWEEP_EINVAL;
+    const int k = tile / (2 * n) - 1;  // Eq. 1
+    if (depth == 0) depth = k - (k % 2);
+    if (depth < 2 || depth > k || (depth % 2) != 0) return SWEEP_EINVAL;
+    sweep_s *h = new (std::nothrow) sweep_s;
+    if (!h) return SWEEP_ENOMEM;
+    h->eqn = eqn;
+    h->nx = nx;
+    h->ny = ny;
+    h->dt = dt;
+    h->dx = dx;
+    h->tile = tile;
+    h->depth = depth;
+    h->alpha = 1.0;
+    h->gamma = 1.4;
+    h->limiter = 0;
+    h->scheme = 0;
+    h->std_tile = 0;
+    h->profile = 0;
+    h->ev_used = 0;
+    const int prefer[] = {eqn == SWEEP_HEAT ? 32 : 16, 16, 8, 24, 12, 64, 48, 40, 20, 10};
+    for (int t : prefer)
+        if (valid_std_tile(h, t)) {
+            h->std_tile = t;
+            break;
+        }
+    if (h->std_tile == 0) {
+        delete h;
+        return SWEEP_EINVAL;
+    }
+    *out = h;
+    return SWEEP_OK;
+}
+
+SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
+{
+    if (!h || !key) return SWEEP_EINVAL;
+    if (!std::strcmp(key, "alpha")) {
+        if (!(std::isfinite(v) && v > 0.0)) return SWEEP_EINVAL;
+        h->alpha = v;
+    } else if (!std::strcmp(key, "gamma")) {
+        if (!(std::isfinite(v) && v > 1.0)) return SWEEP_EINVAL;
+        h->gamma = v;
+    } else if (!std::strcmp(key, "limiter")) {
+        if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
+        h->limiter = (int)v;
+    } else if (!std::strcmp(key, "scheme")) {
+        if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
+        h->scheme = (int)v;
+    } else if (!std::strcmp(key, "standard_tile")) {
+        if (v != std::floor(v) || !valid_std_tile(h, (int)v)) return SWEEP_EINVAL;
+        h->std_tile = (int)v;
+    } else if (!std::strcmp(key, "profile")) {
+        if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
+        h->profile = (int)v;
+        h->ev_used = 0;
+    } else {
+        return SWEEP_EINVAL;
+    }
+    return SWEEP_OK;
+}
+
+SWEEP_API int sweep_get_param(const sweep_t *h, const char *key, double *v)
+{
+    if (!h || !key || !v) return SWEEP_EINVAL;
+    if (!std::strcmp(key, "alpha")) *v = h->alpha;
+    else if (!std::strcmp(key, "gamma")) *v = h->gamma;
+    else if (!std::strcmp(key, "limiter")) *v = h->limiter;
+    else if (!std::strcmp(key, "scheme")) *v = h->scheme;
+    else if (!std::strcmp(key, "standard_tile")) *v = h->std_tile;
+    else if (!std::strcmp(key, "profile")) *v = h->profile;
+    else if (!std::strcmp(key, "tile")) *v = h->tile;
+    else if (!std::strcmp(key, "depth")) *v = h->depth;
+    else if (!std::strcmp(key, "nx")) *v = (double)h->nx;
+    else if (!std::strcmp(key, "ny")) *v = (double)h->ny;
+    else if (!std::strcmp(key, "ncomp")) *v = ncomp(h->eqn);
+    else if (!std::strcmp(key, "radius")) *v = radius(h->eqn);
+    else if (!std::strcmp(key, "r")) *v = (h->alpha * h->dt) / (h->dx * h->dx);
+    else return SWEEP_EINVAL;
+    return SWEEP_OK;
+}
+
+SWEEP_API size_t sweep_workspace_bytes(const sweep_t *h)
+{
+    if (!h) return 0;
+    return kHeader + sizeof(double) * (size_t)slot_elems(h) * (size_t)(h->depth + 1);
+}
+
+SWEEP_API int sweep_run_swept(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws, CUstream_st *stream)
+{
+    const int rc = check_run(h, d_state, nsteps, d_ws);
+    if (rc != SWEEP_OK) return rc;
+    const Params p = make_params(h, d_state, d_ws);
+    if (h->eqn == SWEEP_HEAT) return swept<Heat>(h, p, nsteps, stream);
+    return swept<Euler>(h, p, nsteps, stream);
+}
+
+SWEEP_API int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
+                       CUstream_st *stream)
+{
+    const int rc = check_run(h, d_state, nsteps, d_ws);
+    if (rc != SWEEP_OK) return rc;
+    const Params p = make_params(h, d_state, d_ws);
+    if (h->eqn == SWEEP_HEAT) return standard_steps<Heat>(h, p, nsteps, stream);
+    return standard_steps<Euler>(h, p, nsteps, stream);
+}
+
+SWEEP_API int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds)
+{
+    if (!h || !ms || !launches || nkinds <= 0) return SWEEP_EINVAL;
+    for (int k = 0; k < nkinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        float t = 0.f;
+        if (cudaEventSynchronize(h->ev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess)
+            return SWEEP_ECUDA;
+        const int k = h->ev_kind[i];
+        if (k < nkinds) {
+            ms[k] += t;
+            launches[k] += 1;
+        }
+    }
+    h->ev_used = 0;
+    return SWEEP_OK;
+}
+
+SWEEP_API void sweep_destroy(sweep_t *h)
+{
+    if (!h) return;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+SWEEP_API const char *sweep_error_string(int status)
+{
+    switch (status) {
+    case SWEEP_OK: return "ok";
+    case SWEEP_EINVAL: return "invalid argument";
+    case SWEEP_ENOMEM: return "out of host memory";
+    case SWEEP_ECUDA: return "CUDA error";
+    case SWEEP_ETIMEOUT: return "device wait timed out";
+    case SWEEP_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

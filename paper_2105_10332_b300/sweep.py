@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/sweep.h (libsweep.so).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels
+of libsweep.so.  There is no CPU fallback -- if the library is missing this
+module raises.  PyTorch supplies device memory and streams.
+
+Low-level functions carry the C names (``sweep_create``, ``sweep_run_swept``
+...); ``Solver`` wraps a handle and its workspace.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsweep.so")
+
+SWEEP_HEAT = 0
+SWEEP_EULER = 1
+
+SWEEP_OK = 0
+SWEEP_EINVAL = 1
+SWEEP_ENOMEM = 2
+SWEEP_ECUDA = 3
+SWEEP_ETIMEOUT = 4
+SWEEP_EUNSUPPORTED = 5
+
+# every symbol include/sweep.h declares: name -> (restype, argtypes)
+_c_int, _c_i64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+SIGNATURES = {
+    "sweep_create": (_c_int, [_c_int, _c_i64, _c_i64, _c_dbl, _c_dbl, _c_int, _c_int,
+                              ctypes.POINTER(_vp)]),
+    "sweep_set_param": (_c_int, [_vp, ctypes.c_char_p, _c_dbl]),
+    "sweep_get_param": (_c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(_c_dbl)]),
+    "sweep_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "sweep_run_swept": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "sweep_run_standard": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
+    "sweep_destroy": (None, [_vp]),
+    "sweep_error_string": (ctypes.c_char_p, [_c_int]),
+}
+
+_lib = None
+
+
+class SweepError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, error_string(status), status))
+
+
+def lib():
+    """Load libsweep.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsweep.so is not built; run `python -m paper_2105_10332_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def error_string(status):
+    return lib().sweep_error_string(int(status)).decode()
+
+
+def _check(status, what):
+    if status != SWEEP_OK:
+        raise SweepError(status, what)
+
+
+# ------------------------------------------------------------ C-named wrappers
+
+def sweep_create(eqn, nx, ny, dt, dx, tile, depth=0):
+    h = ctypes.c_void_p()
+    _check(lib().sweep_create(int(eqn), int(nx), int(ny), float(dt), float(dx), int(tile),
+                              int(depth), ctypes.byref(h)), "sweep_create")
+    return h
+
+
+def sweep_set_param(h, key, value):
+    _check(lib().sweep_set_param(h, key.encode(), float(value)), "sweep_set_param(%s)" % key)
+
+
+def sweep_get_param(h, key):
+    v = ctypes.c_double()
+    _check(lib().sweep_get_param(h, key.encode(), ctypes.byref(v)), "sweep_get_param(%s)" % key)
+    return v.value
+
+
+def sweep_workspace_bytes(h):
+    return int(lib().sweep_workspace_bytes(h))
+
+
+def sweep_run_swept(h, state_ptr, nsteps, ws_ptr, stream_ptr):
+    return int(lib().sweep_run_swept(h, state_ptr, int(nsteps), ws_ptr, stream_ptr))
+
+
+def sweep_run_standard(h, state_ptr, nsteps, ws_ptr, stream_ptr):
+    return int(lib().sweep_run_standard(h, state_ptr, int(nsteps), ws_ptr, stream_ptr))
+
+
+def sweep_profile_read(h, nkinds=5):
+    ms = (ctypes.c_double * nkinds)()
+    n = (ctypes.c_int64 * nkinds)()
+    _check(lib().sweep_profile_read(h, ms, n, int(nkinds)), "sweep_profile_read")
+    return list(ms), list(n)
+
+
+def sweep_destroy(h):
+    lib().sweep_destroy(h)
+
+
+KERNEL_KINDS = ("up_pyramid", "bridges", "octahedron", "down_pyramid", "standard")
+
+
+# ------------------------------------------------------------------ Solver
+
+class Solver:
+    """A swept-rule solver for one grid.
+
+    eqn: "heat" or "euler" (or SWEEP_HEAT / SWEEP_EULER).  States are torch
+    float64 tensors of shape [ny, nx] (heat) or [4, ny, nx] (Euler), advanced
+    in place.  Device tensors run on the current torch stream; host tensors
+    are copied to the device and back (the end-to-end path).
+    """
+
+    def __init__(self, eqn, nx, ny, dt, dx, tile, depth=0, **params):
+        if isinstance(eqn, str):
+            eqn = {"heat": SWEEP_HEAT, "euler": SWEEP_EULER}[eqn]
+        self.eqn = eqn
+        self.nx, self.ny = int(nx), int(ny)
+        self._h = sweep_create(eqn, nx, ny, dt, dx, tile, depth)
+        for k, v in params.items():
+            sweep_set_param(self._h, k, v)
+        self.tile = int(self.get("tile"))
+        self.depth = int(self.get("depth"))
+        self.ncomp = int(self.get("ncomp"))
+        self._ws = None
+
+    def get(self, key):
+        return sweep_get_param(self._h, key)
+
+    def set(self, key, value):
+        sweep_set_param(self._h, key, value)
+
+    @property
+    def workspace_bytes(self):
+        return sweep_workspace_bytes(self._h)
+
+    def workspace(self, device):
+        import torch
+        if self._ws is None or self._ws.device != torch.device(device):
+            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def _shape(self):
+        return (self.ny, self.nx) if self.ncomp == 1 else (self.ncomp, self.ny, self.nx)
+
+    def _run(self, fn, state, nsteps, ws=None):
+        import torch
+        if tuple(state.shape) != self._shape() or state.dtype != torch.float64:
+            raise ValueError("state must be float64 of shape %s" % (self._shape(),))
+        if not state.is_cuda:
+            dev = state.new_empty(state.shape, device="cuda")
+            dev.copy_(state, non_blocking=True)
+            self._run(fn, dev, nsteps, ws)
+            state.copy_(dev, non_blocking=False)
+            return state
+        if not state.is_contiguous():
+            raise ValueError("state must be contiguous")
+        ws = self.workspace(state.device) if ws is None else ws
+        stream = torch.cuda.current_stream(state.device).cuda_stream
+        rc = fn(self._h, ctypes.c_void_p(state.data_ptr()), nsteps, ctypes.c_void_p(ws.data_ptr()),
+                ctypes.c_void_p(stream))
+        _check(rc, fn.__name__)
+        return state
+
+    def run_swept(self, state, nsteps, ws=None):
+        """Advance `state` by nsteps with the swept rule (bit-identical to run_standard)."""
+        return self._run(sweep_run_swept, state, nsteps, ws)
+
+    def run_standard(self, state, nsteps, ws=None):
+        """Advance `state` by nsteps with one kernel per RK2 step."""
+        return self._run(sweep_run_standard, state, nsteps, ws)
+
+    def profile(self):
+        """{kind: (total ms, launches)} of the launches recorded since profiling was enabled."""
+        ms, n = sweep_profile_read(self._h, len(KERNEL_KINDS))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            sweep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, validates arguments and sizes its workspace.  No call here
+reaches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2105_10332_b300 import build as sbuild
+from paper_2105_10332_b300 import sweep as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    sbuild.build()
+    return S.lib()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "sweep.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sweep_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = header_functions()
+    assert "sweep_run_swept" in names and "sweep_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in S.SIGNATURES, n
+
+
+def test_create_validates_geometry(L):
+    good = dict(eqn=S.SWEEP_HEAT, nx=64, ny=64, dt=1e-5, dx=1 / 64, tile=16, depth=6)
+    h = S.sweep_create(**good)
+    assert S.sweep_get_param(h, "depth") == 6
+    S.sweep_destroy(h)
+    bad = [dict(eqn=2), dict(tile=15), dict(tile=2), dict(tile=24), dict(nx=16),
+           dict(depth=7), dict(depth=8), dict(depth=1), dict(dt=0.0), dict(dx=-1.0),
+           dict(dt=float("nan")), dict(eqn=S.SWEEP_EULER, tile=8), dict(eqn=S.SWEEP_EULER, depth=4),
+           dict(eqn=S.SWEEP_EULER, tile=64)]
+    for b in bad:
+        args = dict(good, **b)
+        with pytest.raises(S.SweepError) as e:
+            S.sweep_create(**args)
+        assert e.value.status == S.SWEEP_EINVAL, b
+
+
+def test_depth_zero_picks_largest_even(L):
+    for eqn, tile, expect in ((S.SWEEP_HEAT, 16, 6), (S.SWEEP_HEAT, 32, 14), (S.SWEEP_HEAT, 12, 4),
+                              (S.SWEEP_EULER, 32, 6), (S.SWEEP_EULER, 16, 2), (S.SWEEP_EULER, 20, 4)):
+        h = S.sweep_create(eqn, 4 * tile, 2 * tile, 1e-4, 0.01, tile, 0)
+        assert S.sweep_get_param(h, "depth") == expect
+        S.sweep_destroy(h)
+
+
+def test_params_and_workspace(L):
+    h = S.sweep_create(S.SWEEP_EULER, 96, 64, 1e-3, 0.1, 32, 4)
+    assert S.sweep_get_param(h, "gamma") == 1.4
+    S.sweep_set_param(h, "gamma", 5.0 / 3.0)
+    assert S.sweep_get_param(h, "gamma") == 5.0 / 3.0
+    S.sweep_set_param(h, "limiter", 1)
+    for key, val in (("gamma", 1.0), ("limiter", 2), ("nope", 1.0), ("standard_tile", 7),
+                     ("standard_tile", 48)):
+        with pytest.raises(S.SweepError):
+            S.sweep_set_param(h, key, val)
+    assert S.sweep_get_param(h, "ncomp") == 4 and S.sweep_get_param(h, "radius") == 2
+    # (depth + 1) slots of one state, 256-byte padded, plus a 256-byte header
+    slot = (4 * 96 * 64 * 8 + 255) // 256 * 256
+    assert S.sweep_workspace_bytes(h) == 256 + 5 * slot
+    S.sweep_destroy(h)
+
+
+def test_run_rejects_bad_pointers_before_any_launch(L):
+    h = S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)
+    for fn in (S.sweep_run_swept, S.sweep_run_standard):
+        assert fn(h, None, 1, ctypes.c_void_p(4096), None) == S.SWEEP_EINVAL
+        assert fn(h, ctypes.c_void_p(4096), 1, None, None) == S.SWEEP_EINVAL
+        assert fn(h, ctypes.c_void_p(4104), 1, ctypes.c_void_p(4096), None) == S.SWEEP_EINVAL
+        assert fn(h, ctypes.c_void_p(4096), 1, ctypes.c_void_p(4352 + 8), None) == S.SWEEP_EINVAL
+        assert fn(h, ctypes.c_void_p(4096), -1, ctypes.c_void_p(4096), None) == S.SWEEP_EINVAL
+    S.sweep_destroy(h)
+    assert S.error_string(S.SWEEP_ETIMEOUT) == "device wait timed out"
