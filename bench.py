@@ -40,6 +40,9 @@ FLOPS_PER_CELL_STAGE = {"heat": 7, "euler": 187}
 # (measured: 565 G FMA/s at 1.94 GHz) x 2 flops x 2032 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands (profiles/); an entry is removed whenever that kernel changes.
+TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9249024 + 0}
 
 
 def workload(name):
@@ -294,7 +297,8 @@ def run_ours(args, wl):
     flops = dom_cells * FLOPS_PER_CELL_STAGE[wl["eqn"]]
     achieved = flops / (dom_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": TRAFFIC_PER_LAUNCH.get((wl["name"], dom)),
                 "kernel": dom, "launch_ms": round(dom_ms, 5),
                 "flops_per_launch": flops, "peak_basis": "FP64 148 SMs x 2 FMA/clk x 2032 MHz (derived)",
                 "kernels": {k: {"ms_total": round(v[0], 4), "launches": v[1]} for k, v in prof.items()}}
