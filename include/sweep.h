@@ -125,6 +125,39 @@ int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
                        struct CUstream_st *stream);
 
 /*
+ * Allocation-free form of sweep_run_swept (the paper has no counterpart;
+ * this is an interface convenience).
+ *
+ * For callers that cannot allocate device memory when they advance a state,
+ * e.g. a plug-in inside an application that owns all GPU memory through its
+ * own pool, or a latency-critical loop where an allocation or its failure
+ * mid-run is not acceptable.  Instead of a caller workspace, the level store
+ * lives in a fixed device array of SWEEP_STATIC_SCRATCH_BYTES inside the
+ * library.  Every GPU on which the library is loaded holds that array until
+ * the process exits.
+ *
+ *   - Same arguments and result as sweep_run_swept minus d_ws.  The state is
+ *     still caller-owned device memory, and the current device must be the
+ *     device of the state and the stream.
+ *   - Returns SWEEP_EINVAL when sweep_workspace_bytes(h) exceeds
+ *     SWEEP_STATIC_SCRATCH_BYTES (e.g. Euler 256 x 256 at depth 6 needs
+ *     14 MiB and fits; heat 1024 x 1024 at depth 14 needs 120 MiB and does
+ *     not), and SWEEP_EUNSUPPORTED while "profile" is on.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it.  Make that first call before
+ *     any stream capture.
+ *   - All calls share the one array, which keeps what the last call left
+ *     there.  Nothing in it needs to start at zero: a swept run writes every
+ *     value of the level store before reading it.  Calls that overlap on the
+ *     GPU (on any streams of the same device) race on the array and give
+ *     wrong results; serialise them.
+ */
+#define SWEEP_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+int sweep_run_swept_static(sweep_t *h, double *d_state, int64_t nsteps,
+                           struct CUstream_st *stream);
+
+/*
  * Per-kernel device time of the launches recorded since "profile" was set
  * or since the last read.  Kinds: 0 Up-Pyramid, 1 Bridges, 2 Octahedron,
  * 3 Down-Pyramid, 4 Standard step.  ms[k] receives the summed event time of

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -365,6 +366,50 @@ SWEEP_API const char *sweep_error_string(int status)
     case SWEEP_EUNSUPPORTED: return "unsupported";
     default: return "unknown status";
     }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free swept run.
+//
+// Some callers cannot allocate device memory at the point where they want to
+// advance a state: a host application that owns every byte of the GPU through
+// its own pool and lets plug-ins allocate nothing, or a timing-critical loop
+// in which an allocation (its latency, or its failing halfway through a run)
+// is not acceptable.  For them the level store lives in this fixed array
+// instead of a caller-provided workspace.  The array exists on every GPU that
+// loads this library, for the life of the process.
+//
+// In host code `sweep_static_scratch` only names a host-side stand-in; its
+// device address comes from cudaGetSymbolAddress, taken once per device (with
+// that device current) and cached in static_scratch_ptr.
+static __device__ __align__(256) unsigned char sweep_static_scratch[SWEEP_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex static_scratch_mu;
+void *static_scratch_ptr[kMaxDevices];
+}  // namespace
+
+SWEEP_API int sweep_run_swept_static(sweep_t *h, double *d_state, int64_t nsteps,
+                                     CUstream_st *stream)
+{
+    if (!h || !d_state || nsteps < 0 || !aligned(d_state, 16)) return SWEEP_EINVAL;
+    if (h->profile) return SWEEP_EUNSUPPORTED;  // profiling creates CUDA events
+    if (sweep_workspace_bytes(h) > SWEEP_STATIC_SCRATCH_BYTES) return SWEEP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SWEEP_ECUDA;
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(static_scratch_mu);
+        if (!static_scratch_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, sweep_static_scratch) != cudaSuccess || !p)
+                return SWEEP_ECUDA;
+            static_scratch_ptr[dev] = p;
+        }
+        ws = static_scratch_ptr[dev];
+    }
+    return sweep_run_swept(h, d_state, nsteps, ws, stream);
 }
 
 }  // extern "C"

@@ -33,6 +33,7 @@ SIGNATURES = {
     "sweep_workspace_bytes": (ctypes.c_size_t, [_vp]),
     "sweep_run_swept": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "sweep_run_standard": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "sweep_run_swept_static": (_c_int, [_vp, _vp, _c_i64, _vp]),
     "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
     "sweep_destroy": (None, [_vp]),
     "sweep_error_string": (ctypes.c_char_p, [_c_int]),
@@ -100,6 +101,14 @@ def sweep_run_swept(h, state_ptr, nsteps, ws_ptr, stream_ptr):
 
 def sweep_run_standard(h, state_ptr, nsteps, ws_ptr, stream_ptr):
     return int(lib().sweep_run_standard(h, state_ptr, int(nsteps), ws_ptr, stream_ptr))
+
+
+def sweep_run_swept_static(h, state_ptr, nsteps, stream_ptr):
+    """Swept run with the library's fixed device scratch (no workspace, no allocation)."""
+    return int(lib().sweep_run_swept_static(h, state_ptr, int(nsteps), stream_ptr))
+
+
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 def sweep_profile_read(h, nkinds=5):
