@@ -2,8 +2,9 @@
 //
 // Geometry (Sec. 3.3; levels are RK stages, n the radius of one stage, b the
 // block edge, d the levels one phase advances, 2 <= d <= b/(2n) - 1 (Eq. 1),
-// d even).  Every kernel below gives one CTA a b x b window of the periodic
-// grid and takes one shape through its levels inside shared memory:
+// d even).  Every kernel below gives a b x b window of the periodic grid to
+// one CTA, or to a thread-block cluster of C CTAs, and takes one shape
+// through its levels inside shared memory:
 //
 //   Up-Pyramid   window = block of the grid (offset o = 0 or b/2 in x and y)
 //                level base+s covers [sn, b-sn)^2 of the window
@@ -21,10 +22,19 @@
 // other shape reads -- the 2n-wide frame of every Up-Pyramid level, the two
 // 2n-wide bands along a Bridge's seam, and the top level of each shape -- and
 // reads and writes only cells of its own window, and the windows of one
-// launch partition the plane, so no two CTAs of a launch touch the same word
-// of a slot.  Within the CTA the full-step levels live in buffer F and the
+// launch partition the plane, so no two clusters of a launch touch the same
+// word of a slot.  Within a CTA the full-step levels live in buffer F and the
 // stage levels in buffer H; a second stage updates F in place.
+//
+// Clusters: with C > 1 every CTA of the cluster keeps a full copy of F and H;
+// CTA r computes the r-th of C row bands of each level, writes the new values
+// into its own buffers and, through distributed shared memory, into every
+// peer's, and the cluster barrier at the end of the level makes them visible.
+// Each CTA's scratch (pressures, limiter factors, face fluxes) covers only its
+// band, so a cluster takes the shape's levels in 1/C of the time per level.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include <cstdint>
 
@@ -32,7 +42,12 @@
 
 namespace sweep {
 
-constexpr int kThreads = 256;
+namespace cg = cooperative_groups;
+
+#ifndef SWEEP_THREADS
+#define SWEEP_THREADS 256
+#endif
+constexpr int kThreads = SWEEP_THREADS;  // threads per CTA
 
 struct Rect {
     int x0, x1, y0, y1;
@@ -43,6 +58,19 @@ struct Rect {
 };
 
 __device__ __forceinline__ Rect grow(Rect r, int g) { return {r.x0 - g, r.x1 + g, r.y0 - g, r.y1 + g}; }
+
+// rows [ya, yb) of R: the part of R a CTA of rank r in a cluster of C takes
+__device__ __forceinline__ Rect band(Rect R, int r, int C)
+{
+    const int H = R.h(), q = H / C, m = H % C;
+    const int ya = R.y0 + r * q + (r < m ? r : m);
+    return {R.x0, R.x1, ya, ya + q + (r < m ? 1 : 0)};
+}
+
+__device__ __forceinline__ Rect clip_rows(Rect R, int ya, int yb)
+{
+    return {R.x0, R.x1, R.y0 > ya ? R.y0 : ya, R.y1 < yb ? R.y1 : yb};
+}
 
 // Launch parameters shared by every kernel (passed by value).
 struct Params {
@@ -70,27 +98,42 @@ struct Euler {
     static constexpr int N = 2;
 };
 
+// Rows of the largest band a CTA computes: regions lie inside [n, wp-n), so
+// they are at most wp - 2n rows high, split over C CTAs.
+__host__ __device__ constexpr int band_rows(int wp, int n, int C) { return (wp - 2 * n + C - 1) / C; }
+
+// Euler scratch layout (doubles), for window wp and cluster size C:
+//   P    (rows+4) x wp      cell pressures, band rows +-2
+//   HXP, HXM  rows x wp     half limiter factors along x
+//   HYP, HYM  (rows+2) x wp half limiter factors along y, band rows +-1
+//   FX   4 x rows x (wp-2n+1)   x-face fluxes
+//   FY   4 x (rows+1) x (wp-2n) y-face fluxes
+__host__ __device__ constexpr size_t euler_scratch(int wp, int C)
+{
+    const int r = band_rows(wp, 2, C);
+    return (size_t)(r + 4) * wp + (size_t)2 * r * wp + (size_t)2 * (r + 2) * wp +
+           (size_t)4 * r * (wp - 3) + (size_t)4 * (r + 1) * (wp - 4);
+}
+
 // shared-memory bytes of one CTA with window edge wp
 template <class EQ>
-__host__ __device__ constexpr size_t smem_bytes(int wp)
+__host__ __device__ constexpr size_t smem_bytes(int wp, int C)
 {
     if (EQ::NC == 1)
         return sizeof(double) * 2 * (size_t)wp * wp;
-    // F, H (4 comps each), P, four limiter halves, x and y face fluxes
-    return sizeof(double) * ((size_t)8 * wp * wp + (size_t)wp * wp + (size_t)4 * wp * wp +
-                             (size_t)8 * wp * (wp + 1));
+    return sizeof(double) * ((size_t)8 * wp * wp + euler_scratch(wp, C));
 }
 
 // Per-CTA view of shared memory.
-template <class EQ>
+template <class EQ, int C>
 struct Block {
-    double *buf[2];  // F (even levels), H (odd levels): [NC][wp*wp]
-    double *P;       // Euler: cell pressure [wp*wp]
-    double *hxp, *hxm, *hyp, *hym;  // Euler: half limiter factors [wp*wp]
-    double *fx, *fy;                // Euler: face fluxes [4][wp*(wp+1)]
+    double *buf[2];               // F (even levels), H (odd levels): [NC][wp*wp]
+    double *peer[C > 1 ? C : 1];  // Euler/heat: base of each peer's shared buffer (C > 1)
+    double *P, *hxp, *hxm, *hyp, *hym, *fx, *fy;  // Euler scratch
     int wp;          // window pitch (edge)
-    int64_t ox, oy;  // global origin of the window
     int plane;       // wp*wp
+    int rank;        // rank in the cluster
+    int64_t ox, oy;  // global origin of the window
 
     __device__ void carve(double *smem, int wp_)
     {
@@ -98,24 +141,53 @@ struct Block {
         plane = wp * wp;
         buf[0] = smem;
         buf[1] = smem + EQ::NC * plane;
-        double *p = smem + 2 * EQ::NC * plane;
-        if (EQ::NC == 4) {
+        rank = 0;
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            rank = (int)cl.block_rank();
+            for (int r = 0; r < C; ++r)
+                peer[r] = cl.map_shared_rank(smem, r);
+        }
+        if constexpr (EQ::NC == 4) {
+            const int rows = band_rows(wp, EQ::N, C);
+            double *p = smem + 2 * EQ::NC * plane;
             P = p;
-            p += plane;
+            p += (rows + 4) * wp;
             hxp = p;
-            p += plane;
+            p += rows * wp;
             hxm = p;
-            p += plane;
+            p += rows * wp;
             hyp = p;
-            p += plane;
+            p += (rows + 2) * wp;
             hym = p;
-            p += plane;
+            p += (rows + 2) * wp;
             fx = p;
-            p += 4 * wp * (wp + 1);
+            p += 4 * rows * (wp - 3);
             fy = p;
         }
     }
+    // value v of component c at smem index i of the buffer of `level`: into
+    // this CTA's copy and every peer's
+    __device__ __forceinline__ void put(int64_t level, int c, int i, double v)
+    {
+        const int off = (int)(level & 1) * EQ::NC * plane + c * plane + i;
+        buf[0][off] = v;
+        if constexpr (C > 1) {
+#pragma unroll
+            for (int r = 0; r < C; ++r)
+                if (r != rank) peer[r][off] = v;
+        }
+    }
 };
+
+template <int C>
+__device__ __forceinline__ void level_barrier()
+{
+    if constexpr (C > 1)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
+}
 
 __device__ __forceinline__ int64_t gidx(const Params &p, int64_t ox, int64_t oy, int x, int y)
 {
@@ -133,29 +205,34 @@ __device__ __forceinline__ int64_t gidx(const Params &p, int64_t ox, int64_t oy,
 template <class F>
 __device__ __forceinline__ void for_diff(Rect O, Rect I, F &&f)
 {
-    Rect part[4];
-    int np = 0;
     if (O.empty())
         return;
     if (I.empty()) {
-        part[np++] = O;
-    } else {
-        part[np++] = {O.x0, O.x1, O.y0, I.y0};  // below I
-        part[np++] = {O.x0, O.x1, I.y1, O.y1};  // above I
-        part[np++] = {O.x0, I.x0, I.y0, I.y1};  // left of I
-        part[np++] = {I.x1, O.x1, I.y0, I.y1};  // right of I
+        const int w = O.w(), total = O.area();
+        for (int q = threadIdx.x; q < total; q += blockDim.x)
+            f(O.x0 + q % w, O.y0 + q / w);
+        return;
     }
-    int total = 0;
-    for (int k = 0; k < np; ++k)
-        total += part[k].area();
+    // below I, above I (full width), left of I, right of I
+    const int wo = O.w();
+    const int a0 = wo * (I.y0 - O.y0);
+    const int a1 = a0 + wo * (O.y1 - I.y1);
+    const int wl = I.x0 - O.x0, wr = O.x1 - I.x1, hi = I.h();
+    const int a2 = a1 + wl * hi;
+    const int total = a2 + wr * hi;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        int r = q, k = 0;
-        while (r >= part[k].area()) {
-            r -= part[k].area();
-            ++k;
+        if (q < a0) {
+            f(O.x0 + q % wo, O.y0 + q / wo);
+        } else if (q < a1) {
+            const int r = q - a0;
+            f(O.x0 + r % wo, I.y1 + r / wo);
+        } else if (q < a2) {
+            const int r = q - a1;
+            f(O.x0 + r % wl, I.y0 + r / wl);
+        } else {
+            const int r = q - a2;
+            f(I.x1 + r % wr, I.y0 + r / wr);
         }
-        const int w = part[k].w();
-        f(part[k].x0 + r % w, part[k].y0 + r / w);
     }
 }
 
@@ -172,10 +249,22 @@ __device__ __forceinline__ double *slot_ptr(const Params &p, int64_t level)
     return p.ws + (level % (p.d + 1)) * p.slot_elems;
 }
 
-// level-store traffic of one CTA
-template <class EQ>
-__device__ __forceinline__ void load_level(const Params &p, Block<EQ> &B, int64_t level, Rect O,
-                                           Rect I)
+// 8-byte asynchronous global -> shared copy (cp.async), and the wait for all
+// of this thread's outstanding copies
+__device__ __forceinline__ void cp_async8(double *smem_dst, const double *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// level-store traffic of one CTA (loads go to this CTA's copy only)
+template <class EQ, int C>
+__device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &B, int64_t level,
+                                                 Rect O, Rect I)
 {
     const double *src = slot_ptr(p, level);
     double *dst = B.buf[level & 1];
@@ -184,12 +273,12 @@ __device__ __forceinline__ void load_level(const Params &p, Block<EQ> &B, int64_
         const int64_t g = gidx(p, B.ox, B.oy, x, y);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
-            dst[c * B.plane + y * B.wp + x] = src[c * gplane + g];
+            cp_async8(dst + c * B.plane + y * B.wp + x, src + c * gplane + g);
     });
 }
 
-template <class EQ>
-__device__ __forceinline__ void store_level(const Params &p, Block<EQ> &B, int64_t level, Rect O,
+template <class EQ, int C>
+__device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, int64_t level, Rect O,
                                             Rect I)
 {
     double *dst = slot_ptr(p, level);
@@ -205,130 +294,150 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ> &B, int64
 
 // -------------------------------------------------------------- stage kernels
 
-// Advance region R to `level` (RK2: odd levels are first stages, even levels
-// second stages).  Reads buf[(level-1)&1] on R grown by n, and for a second
-// stage the cell's own value two levels back, which sits in buf[level&1].
-template <class EQ>
-__device__ void stage_region(const Params &p, Block<EQ> &B, int64_t level, Rect R);
+// Advance this CTA's band of region R to `level` (RK2: odd levels are first
+// stages, even levels second stages).  Reads buf[(level-1)&1] on the band
+// grown by n, and for a second stage the cell's own value two levels back,
+// which sits in buf[level&1].  Results go to every CTA of the cluster; the
+// caller ends the level with level_barrier<C>().
+template <class EQ, int C>
+struct Stage;
 
-template <>
-__device__ void stage_region<Heat>(const Params &p, Block<Heat> &B, int64_t level, Rect R)
-{
-    const bool second = (level & 1) == 0;
-    const double *src = B.buf[(level - 1) & 1];
-    double *dst = B.buf[level & 1];
-    const double *own = second ? dst : src;
-    const double c = second ? p.c2 : p.c1;
-    const int wp = B.wp;
-    for_rect(R, [&](int x, int y) {
-        const int i = y * wp + x;
-        dst[i] = heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c);
-    });
-}
-
-template <>
-__device__ void stage_region<Euler>(const Params &p, Block<Euler> &B, int64_t level, Rect R)
-{
-    const bool second = (level & 1) == 0;
-    const double *src = B.buf[(level - 1) & 1];
-    double *dst = B.buf[level & 1];
-    const double *own = second ? dst : src;
-    const double lam = second ? p.c2 : p.c1;
-    const int wp = B.wp, pl = B.plane;
-    const EulerConst k = p.ek;
-    if (R.empty())
-        return;
-
-    // (a) cell pressures on the cross R (+-2 in x on R's rows, +-2 in y on R's columns)
+template <int C>
+struct Stage<Heat, C> {
+    __device__ static void run(const Params &p, Block<Heat, C> &B, int64_t level, Rect R)
     {
-        const Rect rx = {R.x0 - 2, R.x1 + 2, R.y0, R.y1};
-        const Rect ry = {R.x0, R.x1, R.y0 - 2, R.y1 + 2};
-        for_diff(ry, R, [&](int x, int y) {
+        const bool second = (level & 1) == 0;
+        const double *src = B.buf[(level - 1) & 1];
+        const double *own = second ? B.buf[level & 1] : src;
+        const double c = second ? p.c2 : p.c1;
+        const int wp = B.wp;
+        for_rect(band(R, B.rank, C), [&](int x, int y) {
             const int i = y * wp + x;
-            B.P[i] = cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
-        });
-        for_rect(rx, [&](int x, int y) {
-            const int i = y * wp + x;
-            B.P[i] = cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
+            B.put(level, 0, i,
+                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c));
         });
     }
-    __syncthreads();
-    // (b) half limiter factors: x on [x0-1, x1+1) x R.y, y on R.x x [y0-1, y1+1)
+};
+
+template <int C>
+struct Stage<Euler, C> {
+    __device__ static void run(const Params &p, Block<Euler, C> &B, int64_t level, Rect R)
     {
-        const Rect lx = {R.x0 - 1, R.x1 + 1, R.y0, R.y1};
-        const Rect ly = {R.x0, R.x1, R.y0 - 1, R.y1 + 1};
-        const int nlx = lx.area(), total = nlx + ly.area();
-        for (int q = threadIdx.x; q < total; q += blockDim.x) {
-            if (q < nlx) {
-                const int x = lx.x0 + q % lx.w(), y = lx.y0 + q / lx.w();
+        const bool second = (level & 1) == 0;
+        const double *src = B.buf[(level - 1) & 1];
+        const double *own = second ? B.buf[level & 1] : src;
+        const double lam = second ? p.c2 : p.c1;
+        const int wp = B.wp, pl = B.plane;
+        const EulerConst k = p.ek;
+        const Rect S = band(R, B.rank, C);  // this CTA's rows
+        const bool idle = S.empty();
+        const int ya = S.y0;
+        // scratch row origins
+        const int py0 = ya - 2;  // P rows [ya-2, yb+2)
+        const int hy0 = ya - 1;  // HY rows [ya-1, yb+1)
+
+        // (a) cell pressures: S's rows +-2 in x, and 2 rows above and below S
+        if (!idle) {
+            const Rect rx = {S.x0 - 2, S.x1 + 2, S.y0, S.y1};
+            const Rect ry = {S.x0, S.x1, S.y0 - 2, S.y1 + 2};
+            for_diff(ry, S, [&](int x, int y) {
                 const int i = y * wp + x;
-                const double pc = B.P[i];
-                limiter_halves(__dadd_rn(pc, -B.P[i - 1]), __dadd_rn(B.P[i + 1], -pc), p.literal,
-                               B.hxp[i], B.hxm[i]);
-            } else {
-                const int r = q - nlx;
-                const int x = ly.x0 + r % ly.w(), y = ly.y0 + r / ly.w();
+                B.P[(y - py0) * wp + x] =
+                    cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
+            });
+            for_rect(rx, [&](int x, int y) {
                 const int i = y * wp + x;
-                const double pc = B.P[i];
-                limiter_halves(__dadd_rn(pc, -B.P[i - wp]), __dadd_rn(B.P[i + wp], -pc),
-                               p.literal, B.hyp[i], B.hym[i]);
+                B.P[(y - py0) * wp + x] =
+                    cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
+            });
+        }
+        __syncthreads();
+        // (b) half limiter factors: x on [x0-1, x1+1) x S.rows, y on S.cols x [ya-1, yb+1)
+        if (!idle) {
+            const Rect lx = {S.x0 - 1, S.x1 + 1, S.y0, S.y1};
+            const Rect ly = {S.x0, S.x1, S.y0 - 1, S.y1 + 1};
+            const int nlx = lx.area(), total = nlx + ly.area();
+            for (int q = threadIdx.x; q < total; q += blockDim.x) {
+                if (q < nlx) {
+                    const int x = lx.x0 + q % lx.w(), y = lx.y0 + q / lx.w();
+                    const int j = (y - py0) * wp + x;
+                    const double pc = B.P[j];
+                    const int o = (y - ya) * wp + x;
+                    limiter_halves(__dadd_rn(pc, -B.P[j - 1]), __dadd_rn(B.P[j + 1], -pc),
+                                   p.literal, B.hxp[o], B.hxm[o]);
+                } else {
+                    const int r = q - nlx;
+                    const int x = ly.x0 + r % ly.w(), y = ly.y0 + r / ly.w();
+                    const int j = (y - py0) * wp + x;
+                    const double pc = B.P[j];
+                    const int o = (y - hy0) * wp + x;
+                    limiter_halves(__dadd_rn(pc, -B.P[j - wp]), __dadd_rn(B.P[j + wp], -pc),
+                                   p.literal, B.hyp[o], B.hym[o]);
+                }
             }
         }
-    }
-    __syncthreads();
-    // (c) face fluxes: x faces f = x0..x1 on each row (between f-1 and f),
-    //     y faces g = y0..y1 on each column (between g-1 and g)
-    const int W = R.w(), Hh = R.h();
-    const int fxw = W + 1;           // x faces per row
-    const int nfx = fxw * Hh;        // x faces
-    const int nfy = W * (Hh + 1);    // y faces
-    const int fpl = wp * (wp + 1);   // face-array plane
-    {
-        const int total = nfx + nfy;
-        for (int q = threadIdx.x; q < total; q += blockDim.x) {
-            double fh[4];
-            if (q < nfx) {
-                const int fo = q % fxw, yo = q / fxw;
-                const int x = R.x0 + fo, y = R.y0 + yo;
-                const int i0 = y * wp + x - 1, i1 = i0 + 1;
-                const double q0[4] = {src[i0], src[pl + i0], src[2 * pl + i0], src[3 * pl + i0]};
-                const double q1[4] = {src[i1], src[pl + i1], src[2 * pl + i1], src[3 * pl + i1]};
-                face_flux(q0, q1, B.hxp[i0], B.hxm[i1], k, fh);
-                const int o = yo * fxw + fo;
+        __syncthreads();
+        // (c) face fluxes: x faces f = x0..x1 on S's rows (between f-1 and f),
+        //     y faces g = ya..yb on S's columns (between g-1 and g)
+        const int W = S.w(), Hh = S.h();
+        const int fxw = W + 1;
+        const int nfx = fxw * Hh;
+        const int nfy = W * (Hh + 1);
+        const int rows = band_rows(wp, Euler::N, C);
+        const int fxpl = rows * (wp - 3);        // x-flux component plane
+        const int fypl = (rows + 1) * (wp - 4);  // y-flux component plane
+        if (!idle) {
+            const int total = nfx + nfy;
+            for (int q = threadIdx.x; q < total; q += blockDim.x) {
+                double fh[4];
+                if (q < nfx) {
+                    const int fo = q % fxw, yo = q / fxw;
+                    const int x = S.x0 + fo, y = S.y0 + yo;
+                    const int i0 = y * wp + x - 1, i1 = i0 + 1;
+                    const double q0[4] = {src[i0], src[pl + i0], src[2 * pl + i0], src[3 * pl + i0]};
+                    const double q1[4] = {src[i1], src[pl + i1], src[2 * pl + i1], src[3 * pl + i1]};
+                    const int h0 = yo * wp + x - 1;
+                    face_flux(q0, q1, B.hxp[h0], B.hxm[h0 + 1], k, fh);
+                    const int o = yo * fxw + fo;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        B.fx[c * fxpl + o] = fh[c];
+                } else {
+                    const int r = q - nfx;
+                    const int xo = r % W, go = r / W;
+                    const int x = S.x0 + xo, y = S.y0 + go;
+                    const int i0 = (y - 1) * wp + x, i1 = i0 + wp;
+                    // y-normal frame: (rho, m_y, m_x, E)
+                    const double q0[4] = {src[i0], src[2 * pl + i0], src[pl + i0], src[3 * pl + i0]};
+                    const double q1[4] = {src[i1], src[2 * pl + i1], src[pl + i1], src[3 * pl + i1]};
+                    const int h0 = (y - 1 - hy0) * wp + x;
+                    face_flux(q0, q1, B.hyp[h0], B.hym[h0 + wp], k, fh);
+                    const int o = go * W + xo;
+                    B.fy[o] = fh[0];
+                    B.fy[fypl + o] = fh[2];
+                    B.fy[2 * fypl + o] = fh[1];
+                    B.fy[3 * fypl + o] = fh[3];
+                }
+            }
+        }
+        __syncthreads();
+        // (d) conservative update of S, written to every CTA of the cluster
+        if (!idle) {
+            for_rect(S, [&](int x, int y) {
+                const int i = y * wp + x;
+                const int xo = x - S.x0, yo = y - S.y0;
+                const int ofx = yo * fxw + xo;  // face at x - 1/2
+                const int ofy = yo * W + xo;    // face at y - 1/2
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    B.fx[c * fpl + o] = fh[c];
-            } else {
-                const int r = q - nfx;
-                const int xo = r % W, go = r / W;
-                const int x = R.x0 + xo, y = R.y0 + go;
-                const int i0 = (y - 1) * wp + x, i1 = i0 + wp;
-                // y-normal frame: (rho, m_y, m_x, E)
-                const double q0[4] = {src[i0], src[2 * pl + i0], src[pl + i0], src[3 * pl + i0]};
-                const double q1[4] = {src[i1], src[2 * pl + i1], src[pl + i1], src[3 * pl + i1]};
-                face_flux(q0, q1, B.hyp[i0], B.hym[i1], k, fh);
-                const int o = go * W + xo;
-                B.fy[o] = fh[0];
-                B.fy[fpl + o] = fh[2];
-                B.fy[2 * fpl + o] = fh[1];
-                B.fy[3 * fpl + o] = fh[3];
-            }
+                    B.put(level, c, i,
+                          euler_combine(B.fx[c * fxpl + ofx], B.fx[c * fxpl + ofx + 1],
+                                        B.fy[c * fypl + ofy], B.fy[c * fypl + ofy + W],
+                                        own[c * pl + i], lam));
+            });
         }
     }
-    __syncthreads();
-    // (d) conservative update of R
-    for_rect(R, [&](int x, int y) {
-        const int i = y * wp + x;
-        const int xo = x - R.x0, yo = y - R.y0;
-        const int ofx = yo * fxw + xo;  // face at x - 1/2
-        const int ofy = yo * W + xo;    // face at y - 1/2
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            dst[c * pl + i] = euler_combine(B.fx[c * fpl + ofx], B.fx[c * fpl + ofx + 1],
-                                            B.fy[c * fpl + ofy], B.fy[c * fpl + ofy + W],
-                                            own[c * pl + i], lam);
-    });
-}
+};
 
 // -------------------------------------------------------------- shape engines
 
@@ -366,61 +475,88 @@ __device__ __forceinline__ void export_part(int kind, int n, int s, int d, Rect 
         I = {0, 0, 0, 0};
 }
 
-// Shapes that grow from nothing (Bridges, the lower half of an Octahedron):
-// before each level, fetch from the level store the part of the previous
-// level around the shape that other shapes produced.
-template <class EQ>
-__device__ void run_growing(const Params &p, Block<EQ> &B, int kind, int64_t base)
+// export the part of the level computed by this CTA (its band of R)
+template <class EQ, int C>
+__device__ __forceinline__ void export_band(const Params &p, Block<EQ, C> &B, int kind, int s,
+                                            int64_t level, Rect R)
+{
+    Rect O, I;
+    export_part(kind, EQ::N, s, p.d, R, O, I);
+    const Rect S = band(R, B.rank, C);
+    const Rect Oc = clip_rows(O, S.y0, S.y1);
+    Rect Ic = I.empty() ? I : clip_rows(I, S.y0, S.y1);
+    if (Ic.empty())
+        Ic = {0, 0, 0, 0};
+    store_level(p, B, level, Oc, Ic);
+}
+
+// Everything a growing shape (Bridges, the lower half of an Octahedron)
+// needs from other shapes was written by earlier launches, so it is fetched
+// at once when the kernel starts: the ring of level base+s-1 around the shape
+// at level s, for every s, and for an Octahedron also level base+d outside its
+// lower half (the base of its upper half).  Each value goes to the buffer of
+// its level's parity at its own cell; no two of them share a cell, and none
+// sits where a level computed before its use is written (the rings of one
+// parity grow outwards, the computed regions stay inside them).
+template <class EQ, int C>
+__device__ void preload_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base, bool top)
 {
     const int n = EQ::N, b = p.b, d = p.d;
     Rect prev = {0, 0, 0, 0};
     for (int s = 1; s <= d; ++s) {
+        const Rect R = shape_rect(kind, b, n, s);
+        load_level_async(p, B, base + s - 1, grow(R, n), prev);
+        prev = R;
+    }
+    if (top)
+        load_level_async(p, B, base + d, Rect{0, b, 0, b}, shape_rect(kLower, b, n, d));
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// A shape that grows from nothing, its inputs already preloaded.
+template <class EQ, int C>
+__device__ void run_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base)
+{
+    const int n = EQ::N, b = p.b, d = p.d;
+    for (int s = 1; s <= d; ++s) {
         const int64_t level = base + s;
         const Rect R = shape_rect(kind, b, n, s);
-        load_level(p, B, level - 1, grow(R, n), prev);
-        __syncthreads();
-        stage_region<EQ>(p, B, level, R);
-        __syncthreads();
-        if (kind != kLower) {
-            Rect O, I;
-            export_part(kind, n, s, d, R, O, I);
-            store_level(p, B, level, O, I);
-        }
-        prev = R;
+        Stage<EQ, C>::run(p, B, level, R);
+        level_barrier<C>();
+        if (kind != kLower)
+            export_band(p, B, kind, s, level, R);
     }
 }
 
-// An Up-Pyramid on the window whose level `base` is already in buffer F.
-template <class EQ>
-__device__ void run_pyramid(const Params &p, Block<EQ> &B, int64_t base)
+// An Up-Pyramid on the window whose level `base` is already in buffer F of
+// every CTA of the cluster.
+template <class EQ, int C>
+__device__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 {
     const int n = EQ::N, b = p.b, d = p.d;
-    {
-        Rect O, I;
-        export_part(kUp, n, 0, d, shape_rect(kUp, b, n, 0), O, I);
-        store_level(p, B, base, O, I);
-    }
+    export_band(p, B, kUp, 0, base, shape_rect(kUp, b, n, 0));
     for (int s = 1; s <= d; ++s) {
         const int64_t level = base + s;
         const Rect R = shape_rect(kUp, b, n, s);
-        stage_region<EQ>(p, B, level, R);
-        __syncthreads();
-        Rect O, I;
-        export_part(kUp, n, s, d, R, O, I);
-        store_level(p, B, level, O, I);
+        Stage<EQ, C>::run(p, B, level, R);
+        level_barrier<C>();
+        export_band(p, B, kUp, s, level, R);
     }
 }
 
 // ------------------------------------------------------------------- kernels
+// Grids: one cluster of C consecutive CTAs per shape.
 
 // Up-Pyramid on block (I, J) of the unshifted grid; level 0 is the state.
-template <class EQ>
+template <class EQ, int C>
 __global__ void __launch_bounds__(kThreads) k_up(Params p)
 {
     extern __shared__ double smem[];
-    Block<EQ> B;
+    Block<EQ, C> B;
     B.carve(smem, p.b);
-    const int I = blockIdx.x % p.tiles_x, J = blockIdx.x / p.tiles_x;
+    const int t = blockIdx.x / C;
+    const int I = t % p.tiles_x, J = t / p.tiles_x;
     B.ox = (int64_t)I * p.b;
     B.oy = (int64_t)J * p.b;
     const int64_t gplane = p.nx * p.ny;
@@ -430,61 +566,68 @@ __global__ void __launch_bounds__(kThreads) k_up(Params p)
         for (int c = 0; c < EQ::NC; ++c)
             B.buf[0][c * B.plane + y * B.wp + x] = p.state[c * gplane + g];
     });
-    __syncthreads();
-    run_pyramid<EQ>(p, B, 0);
+    level_barrier<C>();  // also: every CTA of the cluster has started
+    run_pyramid<EQ, C>(p, B, 0);
+    level_barrier<C>();  // no CTA leaves while a peer may still write to it
 }
 
-// X- and Y-Bridges on the seams of the grid with offset o; CTA 2t is the
-// X-Bridge right of block t, CTA 2t+1 the Y-Bridge above it.
-template <class EQ>
+// X- and Y-Bridges on the seams of the grid with offset o; shape 2t is the
+// X-Bridge right of block t, shape 2t+1 the Y-Bridge above it.
+template <class EQ, int C>
 __global__ void __launch_bounds__(kThreads) k_bridges(Params p, int64_t base, int o)
 {
     extern __shared__ double smem[];
-    Block<EQ> B;
+    Block<EQ, C> B;
     B.carve(smem, p.b);
-    const int t = blockIdx.x >> 1, kind = (blockIdx.x & 1) ? kYBridge : kXBridge;
+    const int sh = blockIdx.x / C;
+    const int t = sh >> 1, kind = (sh & 1) ? kYBridge : kXBridge;
     const int I = t % p.tiles_x, J = t / p.tiles_x;
     const int h = p.b / 2;
     B.ox = (int64_t)I * p.b + o + (kind == kXBridge ? h : 0);
     B.oy = (int64_t)J * p.b + o + (kind == kYBridge ? h : 0);
     if (B.ox >= p.nx) B.ox -= p.nx;
     if (B.oy >= p.ny) B.oy -= p.ny;
-    run_growing<EQ>(p, B, kind, base);
+    preload_growing<EQ, C>(p, B, kind, base, false);
+    if constexpr (C > 1) cg::this_cluster().sync();
+    run_growing<EQ, C>(p, B, kind, base);
+    if constexpr (C > 1) cg::this_cluster().sync();
 }
 
 // Octahedron at the upper-right corner of block (I, J) of the grid with
 // offset o (window = the block of the shifted grid centred on that corner).
 // last != 0 makes it the Down-Pyramid: the lower half only, after which the
 // window, now complete at level base+d, is written to the state.
-template <class EQ>
+template <class EQ, int C>
 __global__ void __launch_bounds__(kThreads) k_octahedron(Params p, int64_t base, int o, int last)
 {
     extern __shared__ double smem[];
-    Block<EQ> B;
+    Block<EQ, C> B;
     B.carve(smem, p.b);
-    const int I = blockIdx.x % p.tiles_x, J = blockIdx.x / p.tiles_x;
+    const int t = blockIdx.x / C;
+    const int I = t % p.tiles_x, J = t / p.tiles_x;
     const int h = p.b / 2;
     B.ox = (int64_t)I * p.b + o + h;
     B.oy = (int64_t)J * p.b + o + h;
     if (B.ox >= p.nx) B.ox -= p.nx;
     if (B.oy >= p.ny) B.oy -= p.ny;
-    run_growing<EQ>(p, B, kLower, base);
+    preload_growing<EQ, C>(p, B, kLower, base, true);
+    if constexpr (C > 1) cg::this_cluster().sync();
+    run_growing<EQ, C>(p, B, kLower, base);
     const int64_t top = base + p.d;
     const Rect whole = {0, p.b, 0, p.b};
-    load_level(p, B, top, whole, shape_rect(kLower, p.b, EQ::N, p.d));
-    __syncthreads();
     if (!last) {
-        run_pyramid<EQ>(p, B, top);
+        run_pyramid<EQ, C>(p, B, top);
     } else {
         const int64_t gplane = p.nx * p.ny;
         const double *src = B.buf[top & 1];
-        for_rect(whole, [&](int x, int y) {
+        for_rect(band(whole, B.rank, C), [&](int x, int y) {
             const int64_t g = gidx(p, B.ox, B.oy, x, y);
 #pragma unroll
             for (int c = 0; c < EQ::NC; ++c)
                 p.state[c * gplane + g] = src[c * B.plane + y * B.wp + x];
         });
     }
+    if constexpr (C > 1) cg::this_cluster().sync();
 }
 
 // One RK2 step of the Standard solver: block (I, J) of edge T = std_tile
@@ -495,7 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *s
 {
     extern __shared__ double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 4 * n;
-    Block<EQ> B;
+    Block<EQ, 1> B;
     B.carve(smem, wp);
     const int tx = (int)(p.nx / T);
     const int I = blockIdx.x % tx, J = blockIdx.x / tx;
@@ -509,9 +652,9 @@ __global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *s
             B.buf[0][c * B.plane + y * wp + x] = src[c * gplane + g];
     });
     __syncthreads();
-    stage_region<EQ>(p, B, 1, {n, wp - n, n, wp - n});
+    Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
-    stage_region<EQ>(p, B, 2, {2 * n, wp - 2 * n, 2 * n, wp - 2 * n});
+    Stage<EQ, 1>::run(p, B, 2, {2 * n, wp - 2 * n, 2 * n, wp - 2 * n});
     __syncthreads();
     for_rect({2 * n, wp - 2 * n, 2 * n, wp - 2 * n}, [&](int x, int y) {
         const int64_t g = gidx(p, B.ox, B.oy, x, y);

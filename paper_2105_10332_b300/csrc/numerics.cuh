@@ -36,7 +36,7 @@ struct EulerConst {
 __device__ __forceinline__ double cell_pressure(double rho, double mx, double my, double E,
                                                 const EulerConst &k)
 {
-    const double inv = __ddiv_rn(1.0, rho);
+    const double inv = __drcp_rn(rho);  // correctly rounded, equal to 1.0 / rho
     const double u = __dmul_rn(mx, inv);
     const double v = __dmul_rn(my, inv);
     const double ke2 = __dadd_rn(__dmul_rn(mx, u), __dmul_rn(my, v));
@@ -85,7 +85,7 @@ __device__ __forceinline__ void limiter_halves(double dm, double dp, int literal
 __device__ __forceinline__ void state_flux(double rho, double mn, double mt, double E,
                                            const EulerConst &k, double f[4], double &lam)
 {
-    const double inv = __ddiv_rn(1.0, rho);
+    const double inv = __drcp_rn(rho);  // correctly rounded, equal to 1.0 / rho
     const double un = __dmul_rn(mn, inv);
     const double ut = __dmul_rn(mt, inv);
     const double ke2 = __fma_rn(mn, un, __dmul_rn(mt, ut));

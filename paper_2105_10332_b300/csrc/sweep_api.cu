@@ -23,6 +23,7 @@ struct sweep_s {
     int limiter;   // 0 textbook orientation, 1 as printed
     int scheme;    // heat: 0 RK2 midpoint, 1 forward Euler
     int std_tile;
+    int cluster;   // CTAs per swept window (1, 2 or 4)
     // optional per-launch event timing ("profile" parameter)
     int profile;
     std::vector<cudaEvent_t> ev;   // start/end pairs, reused across runs
@@ -45,22 +46,24 @@ int64_t slot_elems(const sweep_s *h)
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-// largest shared-memory window the kernels accept
-int max_window(int eqn)
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// shared-memory bytes of a swept CTA / a Standard CTA
+size_t swept_smem(int eqn, int b, int C)
 {
-    int w = 8;
-    while (true) {
-        const size_t s = eqn == SWEEP_HEAT ? smem_bytes<Heat>(w + 2) : smem_bytes<Euler>(w + 2);
-        if (s > 227 * 1024) return w;
-        w += 2;
-    }
+    return eqn == SWEEP_HEAT ? smem_bytes<Heat>(b, C) : smem_bytes<Euler>(b, C);
 }
 
 bool valid_std_tile(const sweep_s *h, int t)
 {
     const int n = radius(h->eqn);
     if (t < 8 || t > 64 || h->nx % t != 0 || h->ny % t != 0) return false;
-    return t + 4 * n <= max_window(h->eqn);
+    return swept_smem(h->eqn, t + 4 * n, 1) <= kMaxSmem;
+}
+
+bool valid_cluster(int eqn, int b, int C)
+{
+    return (C == 1 || C == 2 || C == 4) && swept_smem(eqn, b, C) <= kMaxSmem;
 }
 
 Params make_params(const sweep_s *h, double *state, void *ws)
@@ -138,7 +141,7 @@ int standard_steps(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
 {
     if (nsteps <= 0) return SWEEP_OK;
     const int T = h->std_tile;
-    const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N);
+    const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N, 1);
     if (set_smem(k_standard<EQ>, smem) != cudaSuccess) return SWEEP_ECUDA;
     const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
     double *a = p.state, *b = p.ws;
@@ -160,39 +163,77 @@ int standard_steps(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
     return SWEEP_OK;
 }
 
-template <class EQ>
-int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+// launch one swept kernel with C-CTA clusters
+template <int C, class... KArgs, class... Args>
+cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, size_t smem, cudaStream_t st,
+                   Args... args)
+{
+    if constexpr (C == 1) {
+        kernel<<<shapes, kThreads, smem, st>>>(args...);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(shapes * C, 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, args...);
+    }
+}
+
+template <class EQ, int C>
+int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
 {
     const int64_t L = 2 * nsteps;
     const int d = h->depth;
     int64_t done = 0;
     if (L >= d) {
-        const size_t smem = smem_bytes<EQ>(h->tile);
-        if (set_smem(k_up<EQ>, smem) != cudaSuccess || set_smem(k_bridges<EQ>, smem) != cudaSuccess ||
-            set_smem(k_octahedron<EQ>, smem) != cudaSuccess)
+        const size_t smem = smem_bytes<EQ>(h->tile, C);
+        if (set_smem(k_up<EQ, C>, smem) != cudaSuccess ||
+            set_smem(k_bridges<EQ, C>, smem) != cudaSuccess ||
+            set_smem(k_octahedron<EQ, C>, smem) != cudaSuccess)
             return SWEEP_ECUDA;
         const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
         const int64_t m = L / d - 1;  // whole [Bridges, Octahedron] cycles
+        cudaError_t e;
         {
             Bracket br(h, st, kKindUp);
-            k_up<EQ><<<tiles, kThreads, smem, st>>>(p);
+            e = launch<C>(k_up<EQ, C>, tiles, smem, st, p);
         }
-        for (int64_t c = 0; c <= m; ++c) {
+        for (int64_t c = 0; c <= m && e == cudaSuccess; ++c) {
             const int o = (c & 1) ? h->tile / 2 : 0;
             const int64_t base = c * d;
             {
                 Bracket br(h, st, kKindBridges);
-                k_bridges<EQ><<<2 * tiles, kThreads, smem, st>>>(p, base, o);
+                e = launch<C>(k_bridges<EQ, C>, 2 * tiles, smem, st, p, base, o);
             }
+            if (e != cudaSuccess) break;
             {
                 Bracket br(h, st, c == m ? kKindDown : kKindOctahedron);
-                k_octahedron<EQ><<<tiles, kThreads, smem, st>>>(p, base, o, c == m ? 1 : 0);
+                e = launch<C>(k_octahedron<EQ, C>, tiles, smem, st, p, base, o, c == m ? 1 : 0);
             }
         }
-        if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
+        if (e != cudaSuccess) return SWEEP_ECUDA;
         done = (m + 1) * d;
     }
     return standard_steps<EQ>(h, p, (L - done) / 2, st);
+}
+
+template <class EQ>
+int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    switch (h->cluster) {
+    case 2: return swept_c<EQ, 2>(h, p, nsteps, st);
+    case 4: return swept_c<EQ, 4>(h, p, nsteps, st);
+    default: return swept_c<EQ, 1>(h, p, nsteps, st);
+    }
 }
 
 int check_run(const sweep_t *h, const double *state, int64_t nsteps, const void *ws)
@@ -216,7 +257,8 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     if (eqn != SWEEP_HEAT && eqn != SWEEP_EULER) return SWEEP_EINVAL;
     if (!(std::isfinite(dt) && dt > 0.0 && std::isfinite(dx) && dx > 0.0)) return SWEEP_EINVAL;
     const int n = radius(eqn);
-    if (tile <= 2 * n || (tile % 2) != 0 || tile > max_window(eqn)) return SWEEP_EINVAL;
+    const int cluster = eqn == SWEEP_HEAT ? 1 : 2;
+    if (tile <= 2 * n || (tile % 2) != 0 || !valid_cluster(eqn, tile, cluster)) return SWEEP_EINVAL;
     if (nx <= 0 || ny <= 0 || nx % tile != 0 || ny % tile != 0) return SWEEP_EINVAL;
     if (nx / tile < 2 || ny / tile < 2) return SWEEP_EINVAL;
     if (nx > (int64_t(1) << 31) || ny > (int64_t(1) << 31)) return SWEEP_EINVAL;
@@ -237,6 +279,7 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->limiter = 0;
     h->scheme = 0;
     h->std_tile = 0;
+    h->cluster = cluster;
     h->profile = 0;
     h->ev_used = 0;
     const int prefer[] = {eqn == SWEEP_HEAT ? 32 : 16, 16, 8, 24, 12, 64, 48, 40, 20, 10};
@@ -271,6 +314,9 @@ SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
     } else if (!std::strcmp(key, "standard_tile")) {
         if (v != std::floor(v) || !valid_std_tile(h, (int)v)) return SWEEP_EINVAL;
         h->std_tile = (int)v;
+    } else if (!std::strcmp(key, "cluster")) {
+        if (v != std::floor(v) || !valid_cluster(h->eqn, h->tile, (int)v)) return SWEEP_EINVAL;
+        h->cluster = (int)v;
     } else if (!std::strcmp(key, "profile")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
         h->profile = (int)v;
@@ -290,6 +336,7 @@ SWEEP_API int sweep_get_param(const sweep_t *h, const char *key, double *v)
     else if (!std::strcmp(key, "scheme")) *v = h->scheme;
     else if (!std::strcmp(key, "standard_tile")) *v = h->std_tile;
     else if (!std::strcmp(key, "profile")) *v = h->profile;
+    else if (!std::strcmp(key, "cluster")) *v = h->cluster;
     else if (!std::strcmp(key, "tile")) *v = h->tile;
     else if (!std::strcmp(key, "depth")) *v = h->depth;
     else if (!std::strcmp(key, "nx")) *v = (double)h->nx;

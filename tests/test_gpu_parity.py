@@ -219,3 +219,34 @@ def test_heat_large_sampled_closed_form(torch_cuda):
         G = 1 + z + 0.5 * z * z
         exp += amp * G ** N * np.sin(2 * math.pi * ky * y[js] + phy) * np.sin(2 * math.pi * kx * x[is_] + phx)
     assert np.max(np.abs(got - exp)) <= 1e-12 * np.max(np.abs(u0))
+
+
+# ------------------------------------------------------------------- clusters
+
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("eqn,nx,ny,tile", [("euler", 64, 64, 32), ("euler", 96, 48, 24),
+                                             ("euler", 72, 108, 36), ("heat", 64, 64, 16),
+                                             ("heat", 80, 40, 20)])
+def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, eqn, nx, ny, tile):
+    """A window shared by 1, 2 or 4 CTAs (distributed shared memory) gives the
+    same bits as the oracle for every legal depth and several step counts."""
+    from paper_2105_10332_b300 import sweep as S
+    n = 1 if eqn == "heat" else 2
+    k = tile // (2 * n) - 1
+    for d in range(2, k + 1, 2):
+        if eqn == "euler":
+            s, q0, dt, dx = euler_solver(S, nx, ny, tile, d)
+        else:
+            s, _ = heat_solver(S, nx, ny, tile, d)
+            q0 = W.heat_modes(nx, ny, seed=tile + d)
+        try:
+            s.set("cluster", cluster)
+        except S.SweepError:
+            continue  # window does not fit this cluster size's shared memory
+        for N in (3, 8):
+            if eqn == "euler":
+                ref = oracle_lib.euler_run(q0, dt, dx, N)
+            else:
+                ref = oracle_lib.heat_run(q0, s.get("r"), N)
+            got = gpu_run(torch_cuda, s, q0, N, "run_swept")
+            assert np.array_equal(got, ref), (cluster, d, N, relerr(got, ref))
