@@ -85,6 +85,14 @@ int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile
  *                    reading of the garbled ratio); 1 the orientation as printed
  *   "scheme"         heat time rule: 0 RK2 midpoint, 1 forward Euler (App. A)
  *   "standard_tile"  block edge of the Standard solver (8..64, divides nx, ny)
+ *   "cluster"        CTAs sharing one swept window through distributed shared
+ *                    memory, for every swept kernel (1, 2, 4); "cluster_oct"
+ *                    and "cluster_bridges" set the Up-Pyramid/Octahedron and
+ *                    the Bridge kernels separately.  Defaults: Euler 2 and 1,
+ *                    heat 1 and 1.  A size whose shared memory does not fit
+ *                    is rejected.
+ *   "passes"         row bands each CTA takes one after another per level
+ *                    (1, 2, 4): less shared memory per CTA, more CTAs per SM
  *   "profile"        1: every later run brackets each kernel launch with a
  *                    pair of CUDA events on its stream (read them with
  *                    sweep_profile_read); 0 (default): no events

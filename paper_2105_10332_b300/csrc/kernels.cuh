@@ -30,8 +30,10 @@
 // CTA r computes the r-th of C row bands of each level, writes the new values
 // into its own buffers and, through distributed shared memory, into every
 // peer's, and the cluster barrier at the end of the level makes them visible.
-// Each CTA's scratch (pressures, limiter factors, face fluxes) covers only its
+// Each CTA's scratch (pressures, limiter factors, face fluxes) covers only one
 // band, so a cluster takes the shape's levels in 1/C of the time per level.
+// A CTA may also split its band into `passes` sub-bands taken one after the
+// other, which shrinks the scratch again (two CTAs then fit on one SM).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -85,6 +87,7 @@ struct Params {
     double *state;       // [ncomp][ny][nx]
     double *ws;          // level store: d+1 slots
     int64_t slot_elems;  // doubles per slot (>= ncomp*nx*ny, padded)
+    int passes;          // row bands each CTA takes one after another per level
 };
 
 // ------------------------------------------------------------------ equations
@@ -110,7 +113,7 @@ __host__ __device__ constexpr int band_rows(int wp, int n, int C) { return (wp -
 //   FY   4 x (rows+1) x (wp-2n) y-face fluxes
 __host__ __device__ constexpr size_t euler_scratch(int wp, int C)
 {
-    const int r = band_rows(wp, 2, C);
+    const int r = band_rows(wp, 2, C);  // C: bands per window (cluster size x passes)
     return (size_t)(r + 4) * wp + (size_t)2 * r * wp + (size_t)2 * (r + 2) * wp +
            (size_t)4 * r * (wp - 3) + (size_t)4 * (r + 1) * (wp - 4);
 }
@@ -135,8 +138,11 @@ struct Block {
     int rank;        // rank in the cluster
     int64_t ox, oy;  // global origin of the window
 
-    __device__ void carve(double *smem, int wp_)
+    int bands;       // row bands per level: C x passes
+
+    __device__ void carve(double *smem, int wp_, int passes = 1)
     {
+        bands = C * passes;
         wp = wp_;
         plane = wp * wp;
         buf[0] = smem;
@@ -149,7 +155,7 @@ struct Block {
                 peer[r] = cl.map_shared_rank(smem, r);
         }
         if constexpr (EQ::NC == 4) {
-            const int rows = band_rows(wp, EQ::N, C);
+            const int rows = band_rows(wp, EQ::N, bands);
             double *p = smem + 2 * EQ::NC * plane;
             P = p;
             p += (rows + 4) * wp;
@@ -323,13 +329,20 @@ template <int C>
 struct Stage<Euler, C> {
     __device__ static void run(const Params &p, Block<Euler, C> &B, int64_t level, Rect R)
     {
+        const int np = B.bands / C;
+        for (int k = 0; k < np; ++k) {
+            if (k) __syncthreads();  // the scratch of the previous sub-band is free
+            run_band(p, B, level, band(R, B.rank * np + k, B.bands));
+        }
+    }
+    __device__ static void run_band(const Params &p, Block<Euler, C> &B, int64_t level, Rect S)
+    {
         const bool second = (level & 1) == 0;
         const double *src = B.buf[(level - 1) & 1];
         const double *own = second ? B.buf[level & 1] : src;
         const double lam = second ? p.c2 : p.c1;
         const int wp = B.wp, pl = B.plane;
         const EulerConst k = p.ek;
-        const Rect S = band(R, B.rank, C);  // this CTA's rows
         const bool idle = S.empty();
         const int ya = S.y0;
         // scratch row origins
@@ -383,7 +396,7 @@ struct Stage<Euler, C> {
         const int fxw = W + 1;
         const int nfx = fxw * Hh;
         const int nfy = W * (Hh + 1);
-        const int rows = band_rows(wp, Euler::N, C);
+        const int rows = band_rows(wp, Euler::N, B.bands);
         const int fxpl = rows * (wp - 3);        // x-flux component plane
         const int fypl = (rows + 1) * (wp - 4);  // y-flux component plane
         if (!idle) {
@@ -554,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) k_up(Params p)
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
-    B.carve(smem, p.b);
+    B.carve(smem, p.b, p.passes);
     const int t = blockIdx.x / C;
     const int I = t % p.tiles_x, J = t / p.tiles_x;
     B.ox = (int64_t)I * p.b;
@@ -578,7 +591,7 @@ __global__ void __launch_bounds__(kThreads) k_bridges(Params p, int64_t base, in
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
-    B.carve(smem, p.b);
+    B.carve(smem, p.b, p.passes);
     const int sh = blockIdx.x / C;
     const int t = sh >> 1, kind = (sh & 1) ? kYBridge : kXBridge;
     const int I = t % p.tiles_x, J = t / p.tiles_x;
@@ -602,7 +615,7 @@ __global__ void __launch_bounds__(kThreads) k_octahedron(Params p, int64_t base,
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
-    B.carve(smem, p.b);
+    B.carve(smem, p.b, p.passes);
     const int t = blockIdx.x / C;
     const int I = t % p.tiles_x, J = t / p.tiles_x;
     const int h = p.b / 2;

@@ -61,7 +61,10 @@ __device__ __forceinline__ void limiter_halves(double dm, double dp, int literal
     const unsigned long long ap = bp & 0x7fffffffffffffffull;
     const bool same = ((bm ^ bp) >> 63) == 0 && am != 0 && ap != 0;
     const bool mlt = am < ap;  // |dm| < |dp|
-    const double q = __ddiv_rn(mlt ? dm : dp, mlt ? dp : dm);
+    // Where the factors are 0 the quotient is unused; dividing 1 by 1 there
+    // keeps the division on its fast path (a zero divisor would send the
+    // lane, and with it the warp, through the special-case path).
+    const double q = __ddiv_rn(same ? (mlt ? dm : dp) : 1.0, same ? (mlt ? dp : dm) : 1.0);
     const double hq = __dmul_rn(0.5, q);
     double plus = mlt ? hq : 0.5;
     double minus = mlt ? 0.5 : hq;

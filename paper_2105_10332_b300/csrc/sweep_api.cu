@@ -23,7 +23,9 @@ struct sweep_s {
     int limiter;   // 0 textbook orientation, 1 as printed
     int scheme;    // heat: 0 RK2 midpoint, 1 forward Euler
     int std_tile;
-    int cluster;   // CTAs per swept window (1, 2 or 4)
+    int cluster;     // CTAs per Up-Pyramid / Octahedron window (1, 2 or 4)
+    int cluster_br;  // CTAs per Bridge window (1, 2 or 4)
+    int passes;      // sub-bands per CTA and level (1, 2 or 4)
     // optional per-launch event timing ("profile" parameter)
     int profile;
     std::vector<cudaEvent_t> ev;   // start/end pairs, reused across runs
@@ -66,6 +68,8 @@ bool valid_cluster(int eqn, int b, int C)
     return (C == 1 || C == 2 || C == 4) && swept_smem(eqn, b, C) <= kMaxSmem;
 }
 
+bool valid_passes(int P) { return P == 1 || P == 2 || P == 4; }
+
 Params make_params(const sweep_s *h, double *state, void *ws)
 {
     Params p;
@@ -91,6 +95,7 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     p.state = state;
     p.ws = ws ? (double *)((char *)ws + kHeader) : nullptr;
     p.slot_elems = slot_elems(h);
+    p.passes = h->passes;
     return p;
 }
 
@@ -188,16 +193,17 @@ cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, size_t smem, cudaS
     }
 }
 
-template <class EQ, int C>
+template <class EQ, int C, int CB>
 int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
 {
     const int64_t L = 2 * nsteps;
     const int d = h->depth;
     int64_t done = 0;
     if (L >= d) {
-        const size_t smem = smem_bytes<EQ>(h->tile, C);
+        const size_t smem = smem_bytes<EQ>(h->tile, C * h->passes);
+        const size_t smem_b = smem_bytes<EQ>(h->tile, CB * h->passes);
         if (set_smem(k_up<EQ, C>, smem) != cudaSuccess ||
-            set_smem(k_bridges<EQ, C>, smem) != cudaSuccess ||
+            set_smem(k_bridges<EQ, CB>, smem_b) != cudaSuccess ||
             set_smem(k_octahedron<EQ, C>, smem) != cudaSuccess)
             return SWEEP_ECUDA;
         const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
@@ -212,7 +218,7 @@ int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
             const int64_t base = c * d;
             {
                 Bracket br(h, st, kKindBridges);
-                e = launch<C>(k_bridges<EQ, C>, 2 * tiles, smem, st, p, base, o);
+                e = launch<CB>(k_bridges<EQ, CB>, 2 * tiles, smem_b, st, p, base, o);
             }
             if (e != cudaSuccess) break;
             {
@@ -226,13 +232,23 @@ int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
     return standard_steps<EQ>(h, p, (L - done) / 2, st);
 }
 
+template <class EQ, int C>
+int swept_b(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    switch (h->cluster_br) {
+    case 2: return swept_c<EQ, C, 2>(h, p, nsteps, st);
+    case 4: return swept_c<EQ, C, 4>(h, p, nsteps, st);
+    default: return swept_c<EQ, C, 1>(h, p, nsteps, st);
+    }
+}
+
 template <class EQ>
 int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
 {
     switch (h->cluster) {
-    case 2: return swept_c<EQ, 2>(h, p, nsteps, st);
-    case 4: return swept_c<EQ, 4>(h, p, nsteps, st);
-    default: return swept_c<EQ, 1>(h, p, nsteps, st);
+    case 2: return swept_b<EQ, 2>(h, p, nsteps, st);
+    case 4: return swept_b<EQ, 4>(h, p, nsteps, st);
+    default: return swept_b<EQ, 1>(h, p, nsteps, st);
     }
 }
 
@@ -279,7 +295,11 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->limiter = 0;
     h->scheme = 0;
     h->std_tile = 0;
+    // measured on B300 (Euler vortex 256^2, block 32): Octahedra on 2-CTA
+    // clusters, Bridges on single CTAs
     h->cluster = cluster;
+    h->cluster_br = 1;
+    h->passes = 1;
     h->profile = 0;
     h->ev_used = 0;
     const int prefer[] = {eqn == SWEEP_HEAT ? 32 : 16, 16, 8, 24, 12, 64, 48, 40, 20, 10};
@@ -317,6 +337,16 @@ SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
     } else if (!std::strcmp(key, "cluster")) {
         if (v != std::floor(v) || !valid_cluster(h->eqn, h->tile, (int)v)) return SWEEP_EINVAL;
         h->cluster = (int)v;
+        h->cluster_br = (int)v;
+    } else if (!std::strcmp(key, "cluster_oct")) {
+        if (v != std::floor(v) || !valid_cluster(h->eqn, h->tile, (int)v)) return SWEEP_EINVAL;
+        h->cluster = (int)v;
+    } else if (!std::strcmp(key, "cluster_bridges")) {
+        if (v != std::floor(v) || !valid_cluster(h->eqn, h->tile, (int)v)) return SWEEP_EINVAL;
+        h->cluster_br = (int)v;
+    } else if (!std::strcmp(key, "passes")) {
+        if (v != std::floor(v) || !valid_passes((int)v)) return SWEEP_EINVAL;
+        h->passes = (int)v;
     } else if (!std::strcmp(key, "profile")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
         h->profile = (int)v;
@@ -336,7 +366,9 @@ SWEEP_API int sweep_get_param(const sweep_t *h, const char *key, double *v)
     else if (!std::strcmp(key, "scheme")) *v = h->scheme;
     else if (!std::strcmp(key, "standard_tile")) *v = h->std_tile;
     else if (!std::strcmp(key, "profile")) *v = h->profile;
-    else if (!std::strcmp(key, "cluster")) *v = h->cluster;
+    else if (!std::strcmp(key, "cluster") || !std::strcmp(key, "cluster_oct")) *v = h->cluster;
+    else if (!std::strcmp(key, "cluster_bridges")) *v = h->cluster_br;
+    else if (!std::strcmp(key, "passes")) *v = h->passes;
     else if (!std::strcmp(key, "tile")) *v = h->tile;
     else if (!std::strcmp(key, "depth")) *v = h->depth;
     else if (!std::strcmp(key, "nx")) *v = (double)h->nx;

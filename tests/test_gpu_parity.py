@@ -223,13 +223,14 @@ def test_heat_large_sampled_closed_form(torch_cuda):
 
 # ------------------------------------------------------------------- clusters
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("cluster,passes", [(1, 1), (2, 1), (4, 1), (1, 2), (2, 2), (1, 4)])
 @pytest.mark.parametrize("eqn,nx,ny,tile", [("euler", 64, 64, 32), ("euler", 96, 48, 24),
                                              ("euler", 72, 108, 36), ("heat", 64, 64, 16),
                                              ("heat", 80, 40, 20)])
-def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, eqn, nx, ny, tile):
-    """A window shared by 1, 2 or 4 CTAs (distributed shared memory) gives the
-    same bits as the oracle for every legal depth and several step counts."""
+def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, passes, eqn, nx, ny, tile):
+    """A window shared by 1, 2 or 4 CTAs (distributed shared memory), each
+    taking its rows in 1, 2 or 4 passes, gives the same bits as the oracle for
+    every legal depth and several step counts."""
     from paper_2105_10332_b300 import sweep as S
     n = 1 if eqn == "heat" else 2
     k = tile // (2 * n) - 1
@@ -241,6 +242,7 @@ def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, eqn, nx, n
             q0 = W.heat_modes(nx, ny, seed=tile + d)
         try:
             s.set("cluster", cluster)
+            s.set("passes", passes)
         except S.SweepError:
             continue  # window does not fit this cluster size's shared memory
         for N in (3, 8):
