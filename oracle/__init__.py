@@ -10,6 +10,8 @@ Functions (each follows the passage cited in the C source):
   euler_run      -- App. B Euler scheme: pressure minmod, Rusanov-form flux, RK2
   swept_replay   -- the Sec. 3.3 phase schedule replayed cell by cell with
                     dependency checks (Eq. 1 bounds the depth)
+  heat_adjoint, euler_adjoint -- discrete adjoints (reverse mode) of the two
+                    schemes, with checkpointing for Euler
   face_flux, limiter, state_flux -- single-face pieces used by the pins
 """
 import ctypes
@@ -47,6 +49,11 @@ def lib():
                                           ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.c_int]
         L.oracle_swept_replay.restype = ctypes.c_int
+        L.oracle_heat_adjoint.argtypes = [i64, i64, ctypes.c_double, dp, i64]
+        L.oracle_heat_adjoint.restype = ctypes.c_int
+        L.oracle_euler_adjoint.argtypes = [i64, i64, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, dp, dp, i64, i64]
+        L.oracle_euler_adjoint.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -99,6 +106,25 @@ def swept_replay(eqn, state0, tile, depth, nsteps, c1, c2, gamma=1.4, limiter=0,
         raise RuntimeError("swept replay failed: %s at level %d cell (%d, %d)"
                            % (ERRORS.get(rc, "?"), st[3], st[4], st[5]))
     return s, stats
+
+
+def heat_adjoint(lamT, r, nsteps):
+    """(A^T)^N lamT for the RK2 heat step A (App. A): the gradient of <u_N, lamT> w.r.t. u_0."""
+    lam = np.ascontiguousarray(lamT, dtype=np.float64).copy()
+    ny, nx = lam.shape
+    _check(lib().oracle_heat_adjoint(nx, ny, float(r), _dptr(lam), int(nsteps)), "heat_adjoint")
+    return lam
+
+
+def euler_adjoint(q0, lamT, dt, dx, nsteps, ckpt=64, gamma=1.4, limiter=0):
+    """dL/dQ^0 given lamT = dL/dQ^N for the App. B scheme (checkpoints every ckpt steps)."""
+    q = np.ascontiguousarray(q0, dtype=np.float64)
+    lam = np.ascontiguousarray(lamT, dtype=np.float64).copy()
+    _, ny, nx = q.shape
+    _check(lib().oracle_euler_adjoint(nx, ny, float(dt), float(dx), float(gamma), int(limiter),
+                                      _dptr(q), _dptr(lam), int(nsteps), int(ckpt)),
+           "euler_adjoint")
+    return lam
 
 
 def face_flux(qm1, q0, q1, q2, gamma=1.4, limiter=0):

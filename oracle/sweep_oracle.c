@@ -664,3 +664,336 @@ int oracle_swept_replay(int eqn, int64_t nx, int64_t ny, int64_t b, int d, int64
     free(R.reader);
     return rc;
 }
+
+/* ======================================================================
+ * Discrete adjoints (reverse mode of the schemes above).
+ *
+ * The swept rule only reorders the explicit scheme (Sec. 3.3), so its
+ * gradient is the gradient of the step-by-step scheme.  For a final-state
+ * loss L(Q^N), lam^N = dL/dQ^N and lam^n = (dQ^{n+1}/dQ^n)^T lam^{n+1}.
+ * Non-smooth points (the limiter's switches, max of the wave speeds, |u_n|)
+ * take the derivative of the branch the forward step took.
+ * ====================================================================== */
+
+/* Heat: the step Q' = Q + c2 L(Q + c1 L Q) with symmetric L.  Adjoint step
+ * (order pinned): mu* = c2 * t(lam); lam_n = fma(c1, t(mu*), lam + mu*),
+ * t(u) = fma(-4, u, (u_W + u_E) + (u_S + u_N)). */
+int oracle_heat_adjoint(int64_t nx, int64_t ny, double r, double *lam, int64_t nsteps)
+{
+    if (nx < 3 || ny < 3 || nsteps < 0)
+        return ORACLE_EINVAL;
+    const size_t n = (size_t)(nx * ny);
+    double *ms = (double *)malloc(sizeof(double) * n);
+    double *out = (double *)malloc(sizeof(double) * n);
+    if (!ms || !out) {
+        free(ms);
+        free(out);
+        return ORACLE_ENOMEM;
+    }
+    const double c1 = 0.5 * r;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int64_t j;
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                ms[j * nx + i] = r * heat_t(lam, nx, ny, i, j);
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                const int64_t c = j * nx + i;
+                out[c] = fma(c1, heat_t(ms, nx, ny, i, j), lam[c] + ms[c]);
+            }
+        memcpy(lam, out, sizeof(double) * n);
+    }
+    free(ms);
+    free(out);
+    return ORACLE_OK;
+}
+
+/* --- Euler: reverse mode of one face flux -------------------------------- */
+
+/* adjoint of the cell pressure: P = (gamma-1) fma(-1/2, m_x u + m_y v, E) */
+static void cell_pressure_bar(const double q[4], double gamma, double pbar, double qbar[4])
+{
+    const double inv = 1.0 / q[0];
+    const double u = q[1] * inv, v = q[2] * inv;
+    const double g1 = gamma - 1.0;
+    const double ebar = pbar * g1;
+    const double kbar = -0.5 * g1 * pbar;
+    double mxbar = kbar * u, mybar = kbar * v;
+    const double ubar = kbar * q[1], vbar = kbar * q[2];
+    mxbar += ubar * inv;
+    mybar += vbar * inv;
+    const double invbar = ubar * q[1] + vbar * q[2];
+    qbar[0] += -invbar * inv * inv;
+    qbar[1] += mxbar;
+    qbar[2] += mybar;
+    qbar[3] += ebar;
+}
+
+/* adjoint of state_flux: given fbar[4] and lambar, accumulate qbar[4] */
+static void state_flux_bar(const double q[4], double gamma, const double fbar[4], double lambar,
+                           double qbar[4])
+{
+    const double inv = 1.0 / q[0];
+    const double mn = q[1], mt = q[2], E = q[3];
+    const double un = mn * inv, ut = mt * inv;
+    const double ke2 = fma(mn, un, mt * ut);
+    const double g1 = gamma - 1.0;
+    const double p = g1 * fma(-0.5, ke2, E);
+    const double c = sqrt((gamma * p) * inv);
+    double mnbar = fbar[0], mtbar = 0.0, Ebar = 0.0, unbar = 0.0, utbar = 0.0, pbar = 0.0,
+           invbar = 0.0;
+    /* f1 = mn un + p */
+    mnbar += fbar[1] * un;
+    unbar += fbar[1] * mn;
+    pbar += fbar[1];
+    /* f2 = mt un */
+    mtbar += fbar[2] * un;
+    unbar += fbar[2] * mt;
+    /* f3 = (E + p) un */
+    Ebar += fbar[3] * un;
+    pbar += fbar[3] * un;
+    unbar += fbar[3] * (E + p);
+    /* lam = |un| + c */
+    unbar += un > 0.0 ? lambar : (un < 0.0 ? -lambar : 0.0);
+    const double cbar = lambar;
+    /* c = sqrt(s), s = gamma p inv */
+    const double sbar = c > 0.0 ? cbar / (2.0 * c) : 0.0;
+    pbar += sbar * gamma * inv;
+    invbar += sbar * gamma * p;
+    /* p = g1 (E - ke2/2) */
+    Ebar += pbar * g1;
+    const double kbar = -0.5 * g1 * pbar;
+    /* ke2 = mn un + mt ut */
+    mnbar += kbar * un;
+    unbar += kbar * mn;
+    mtbar += kbar * ut;
+    utbar += kbar * mt;
+    /* un = mn inv, ut = mt inv */
+    mnbar += unbar * inv;
+    invbar += unbar * mn;
+    mtbar += utbar * inv;
+    invbar += utbar * mt;
+    qbar[0] += -invbar * inv * inv;
+    qbar[1] += mnbar;
+    qbar[2] += mtbar;
+    qbar[3] += Ebar;
+}
+
+/* derivatives of one limiter factor with respect to (dm, dp), for the
+ * branch taken: plus = min(dm/dp, 1) or minus = min(dp/dm, 1) where both
+ * differences are nonzero with equal signs */
+static void limiter_grad(int limiter, int plus, double dm, double dp, double *d_dm, double *d_dp)
+{
+    *d_dm = 0.0;
+    *d_dp = 0.0;
+    if (limiter == 2)
+        return;
+    if (!((dm > 0.0 && dp > 0.0) || (dm < 0.0 && dp < 0.0)))
+        return;
+    /* which quotient this factor is: textbook plus = dm/dp, minus = dp/dm;
+     * the printed orientation swaps them */
+    const int over_dp = (limiter == 0) ? plus : !plus; /* factor = dm/dp ? */
+    if (over_dp) {
+        if (dm / dp < 1.0) {
+            *d_dm = 1.0 / dp;
+            *d_dp = -dm / (dp * dp);
+        }
+    } else {
+        if (dp / dm < 1.0) {
+            *d_dp = 1.0 / dm;
+            *d_dm = -dp / (dm * dm);
+        }
+    }
+}
+
+/* Reverse of face_flux at the face between cells 0 and 1 of the line
+ * (-1, 0, 1, 2), states in the face-normal frame.  a[4]: adjoint of the
+ * numerical flux.  Accumulates into qbar[m][4] for m = 0..3 (cells -1..2). */
+static void face_flux_bar(const double *q[4], double gamma, int limiter, const double a[4],
+                          double qbar[4][4])
+{
+    double p[4];
+    for (int m = 0; m < 4; ++m)
+        p[m] = cell_pressure(q[m][0], q[m][1], q[m][2], q[m][3], gamma);
+    double phi0p, phi0m, phi1p, phi1m;
+    limiter_pair(limiter, p[1] - p[0], p[2] - p[1], &phi0p, &phi0m);
+    limiter_pair(limiter, p[2] - p[1], p[3] - p[2], &phi1p, &phi1m);
+    const double hl = 0.5 * phi0p, hr = 0.5 * phi1m;
+    double dq[4], ql[4], qr[4], fl[4], fr[4], laml, lamr;
+    for (int k = 0; k < 4; ++k) {
+        dq[k] = q[2][k] - q[1][k];
+        ql[k] = fma(hl, dq[k], q[1][k]);
+        qr[k] = fma(-hr, dq[k], q[2][k]);
+    }
+    state_flux(ql, gamma, fl, &laml);
+    state_flux(qr, gamma, fr, &lamr);
+    const double r = laml > lamr ? laml : lamr;
+    /* Fh_k = 1/2 (r (ql_k - qr_k) + fl_k + fr_k) */
+    double qlbar[4], qrbar[4], flbar[4], frbar[4], rbar = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        flbar[k] = 0.5 * a[k];
+        frbar[k] = 0.5 * a[k];
+        qlbar[k] = 0.5 * r * a[k];
+        qrbar[k] = -0.5 * r * a[k];
+        rbar += 0.5 * a[k] * (ql[k] - qr[k]);
+    }
+    const double lamlbar = laml > lamr ? rbar : 0.0;
+    const double lamrbar = laml > lamr ? 0.0 : rbar;
+    double sl[4] = {0, 0, 0, 0}, sr[4] = {0, 0, 0, 0};
+    state_flux_bar(ql, gamma, flbar, lamlbar, sl);
+    state_flux_bar(qr, gamma, frbar, lamrbar, sr);
+    for (int k = 0; k < 4; ++k) {
+        qlbar[k] += sl[k];
+        qrbar[k] += sr[k];
+    }
+    /* ql = q0 + hl dq, qr = q1 - hr dq, dq = q1 - q0 */
+    double hlbar = 0.0, hrbar = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        const double dqbar = qlbar[k] * hl - qrbar[k] * hr;
+        hlbar += qlbar[k] * dq[k];
+        hrbar += -qrbar[k] * dq[k];
+        qbar[1][k] += qlbar[k] - dqbar;
+        qbar[2][k] += qrbar[k] + dqbar;
+    }
+    /* hl = phi0p / 2 from (p0 - pm1, p1 - p0); hr = phi1m / 2 from (p1 - p0, p2 - p1) */
+    double pbar[4] = {0, 0, 0, 0}, g_dm, g_dp;
+    limiter_grad(limiter, 1, p[1] - p[0], p[2] - p[1], &g_dm, &g_dp);
+    pbar[1] += 0.5 * hlbar * g_dm;
+    pbar[0] -= 0.5 * hlbar * g_dm;
+    pbar[2] += 0.5 * hlbar * g_dp;
+    pbar[1] -= 0.5 * hlbar * g_dp;
+    limiter_grad(limiter, 0, p[2] - p[1], p[3] - p[2], &g_dm, &g_dp);
+    pbar[2] += 0.5 * hrbar * g_dm;
+    pbar[1] -= 0.5 * hrbar * g_dm;
+    pbar[3] += 0.5 * hrbar * g_dp;
+    pbar[2] -= 0.5 * hrbar * g_dp;
+    for (int m = 0; m < 4; ++m)
+        cell_pressure_bar(q[m], gamma, pbar[m], qbar[m]);
+}
+
+/* out = J^T v for the residual d(Q)_c = (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2}
+ * - Gh_{j+1/2}) of every cell (out is overwritten).  Each face adds its
+ * contribution a = v_{right} - v_{left} through face_flux_bar. */
+static void euler_residual_vjp(const double *q, const double *v, double *out, int64_t nx,
+                               int64_t ny, double gamma, int limiter)
+{
+    const int64_t plane = nx * ny;
+    memset(out, 0, sizeof(double) * (size_t)(4 * plane));
+    for (int axis = 0; axis < 2; ++axis)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                /* face between cell (i,j) and its + neighbour along axis */
+                double cells[4][4];
+                const double *qp[4];
+                int64_t idx[4];
+                for (int m = 0; m < 4; ++m) {
+                    const int64_t ii = axis == 0 ? i - 1 + m : i;
+                    const int64_t jj = axis == 1 ? j - 1 + m : j;
+                    load_cell(q, nx, ny, ii, jj, axis, cells[m]);
+                    qp[m] = cells[m];
+                    idx[m] = wrapi(jj, ny) * nx + wrapi(ii, nx);
+                }
+                /* adjoint of the flux in the face-normal frame */
+                double a[4];
+                const int64_t cl = idx[1], cr = idx[2];
+                for (int k = 0; k < 4; ++k) {
+                    const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
+                    a[k] = v[kk * plane + cr] - v[kk * plane + cl];
+                }
+                double qb[4][4] = {{0}};
+                face_flux_bar(qp, gamma, limiter, a, qb);
+                for (int m = 0; m < 4; ++m)
+                    for (int k = 0; k < 4; ++k) {
+                        const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
+                        out[kk * plane + idx[m]] += qb[m][k];
+                    }
+            }
+}
+
+/* One adjoint RK2 step at Q^n (RK2: Q* = Q + lam1 d(Q), Q' = Q + lam2 d(Q*)):
+ *   mu*  = lam2 J(Q*)^T lam'
+ *   lam  = lam' + mu* + lam1 J(Q)^T mu*                                  */
+static void euler_adjoint_step(const double *q, double *lam, int64_t nx, int64_t ny, double lam1,
+                               double lam2, double gamma, int limiter, double *qs, double *ms,
+                               double *tmp)
+{
+    const int64_t n4 = 4 * nx * ny;
+    euler_stage(nx, ny, lam1, gamma, limiter, q, q, qs); /* Q* */
+    euler_residual_vjp(qs, lam, tmp, nx, ny, gamma, limiter);
+    for (int64_t k = 0; k < n4; ++k)
+        ms[k] = lam2 * tmp[k];
+    euler_residual_vjp(q, ms, tmp, nx, ny, gamma, limiter);
+    for (int64_t k = 0; k < n4; ++k)
+        lam[k] = lam[k] + ms[k] + lam1 * tmp[k];
+}
+
+/* Gradient of L(Q^N) with respect to Q^0.  lam holds dL/dQ^N on entry and
+ * dL/dQ^0 on return.  Forward states are checkpointed every `ckpt` steps and
+ * recomputed step by step inside each segment. */
+int oracle_euler_adjoint(int64_t nx, int64_t ny, double dt, double dx, double gamma, int limiter,
+                         const double *q0, double *lam, int64_t nsteps, int64_t ckpt)
+{
+    if (nx < 5 || ny < 5 || nsteps < 0 || ckpt < 1 || !(dx > 0.0) || limiter < 0 || limiter > 2)
+        return ORACLE_EINVAL;
+    const size_t n4 = (size_t)(4 * nx * ny);
+    const int64_t nseg = (nsteps + ckpt - 1) / ckpt;
+    double *cps = (double *)malloc(sizeof(double) * n4 * (size_t)(nseg > 0 ? nseg : 1));
+    double *seg = (double *)malloc(sizeof(double) * n4 * (size_t)(ckpt + 1));
+    double *qs = (double *)malloc(sizeof(double) * n4);
+    double *ms = (double *)malloc(sizeof(double) * n4);
+    double *tmp = (double *)malloc(sizeof(double) * n4);
+    if (!cps || !seg || !qs || !ms || !tmp) {
+        free(cps);
+        free(seg);
+        free(qs);
+        free(ms);
+        free(tmp);
+        return ORACLE_ENOMEM;
+    }
+    const double lam2 = dt / dx, lam1 = 0.5 * lam2;
+    /* forward pass: checkpoints Q^{s*ckpt} */
+    memcpy(seg, q0, sizeof(double) * n4);
+    for (int64_t s = 0; s < nseg; ++s) {
+        memcpy(cps + (size_t)s * n4, seg, sizeof(double) * n4);
+        const int64_t len = (s + 1) * ckpt <= nsteps ? ckpt : nsteps - s * ckpt;
+        for (int64_t t = 0; t < len; ++t) {
+            euler_stage(nx, ny, lam1, gamma, limiter, seg, seg, qs);
+            euler_stage(nx, ny, lam2, gamma, limiter, qs, seg, tmp);
+            memcpy(seg, tmp, sizeof(double) * n4);
+        }
+    }
+    /* backward pass, segment by segment */
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t len = (s + 1) * ckpt <= nsteps ? ckpt : nsteps - s * ckpt;
+        memcpy(seg, cps + (size_t)s * n4, sizeof(double) * n4);
+        for (int64_t t = 0; t < len - 1; ++t) {
+            double *cur = seg + (size_t)t * n4, *nxt = seg + (size_t)(t + 1) * n4;
+            euler_stage(nx, ny, lam1, gamma, limiter, cur, cur, qs);
+            euler_stage(nx, ny, lam2, gamma, limiter, qs, cur, nxt);
+        }
+        for (int64_t t = len - 1; t >= 0; --t)
+            euler_adjoint_step(seg + (size_t)t * n4, lam, nx, ny, lam1, lam2, gamma, limiter, qs,
+                               ms, tmp);
+    }
+    free(cps);
+    free(seg);
+    free(qs);
+    free(ms);
+    free(tmp);
+    return ORACLE_OK;
+}
+
+/* single-face reverse mode, exposed for the adjoint pins: qbar[16] += the
+ * gradient of <a, Fh(q-1, q0, q1, q2)> with respect to the four states */
+void oracle_face_flux_vjp(const double *qm1, const double *q0, const double *q1, const double *q2,
+                          double gamma, int limiter, const double *a, double *qbar)
+{
+    const double *q[4] = {qm1, q0, q1, q2};
+    double qb[4][4] = {{0}};
+    face_flux_bar(q, gamma, limiter, a, qb);
+    for (int m = 0; m < 4; ++m)
+        for (int k = 0; k < 4; ++k)
+            qbar[4 * m + k] += qb[m][k];
+}
