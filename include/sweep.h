@@ -82,7 +82,10 @@ int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile
  *   "alpha"          heat diffusivity (> 0)
  *   "gamma"          ratio of specific heats (> 1)
  *   "limiter"        0 pressure-ratio minmod, textbook orientation (App. B,
- *                    reading of the garbled ratio); 1 the orientation as printed
+ *                    reading of the garbled ratio); 1 the orientation as printed;
+ *                    2 no limiting (face value = average of the two cells; not
+ *                    a scheme of the paper: a smooth variant for checking the
+ *                    adjoint against finite differences)
  *   "scheme"         heat time rule: 0 RK2 midpoint, 1 forward Euler (App. A)
  *   "standard_tile"  block edge of the Standard solver (8..64, divides nx, ny)
  *   "cluster"        CTAs sharing one swept window through distributed shared
@@ -131,6 +134,29 @@ int sweep_run_swept(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
  */
 int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
                        struct CUstream_st *stream);
+
+/*
+ * Gradient of a final-state loss with respect to the initial state (the
+ * discrete adjoint; reverse mode of the explicit scheme, which the swept
+ * rule only reorders, Sec. 3.3).  d_lamT = dL/dQ^N (device, state layout);
+ * on return d_lam0 = dL/dQ^0.  At the limiter's switches, the max of the
+ * wave speeds and |u_n| the derivative of the branch the forward step took
+ * is used.
+ *   heat:  the step is linear with a symmetric 5-point operator, so the
+ *          adjoint step is again a two-stage stencil update
+ *          (mu* = r t(lam), lam_n = fma(r/2, t(mu*), lam + mu*)) and runs
+ *          through the swept kernels.  d_q0 is not read (may be NULL);
+ *          d_lam0 may equal d_lamT.
+ *   Euler: a forward swept pass from d_q0 keeps a checkpoint every
+ *          ckpt_every steps; each segment is then recomputed one Standard
+ *          step at a time and reversed step by step (face-wise reverse mode
+ *          of the flux, gathered per cell).  d_lam0 must not alias d_lamT.
+ * d_ws: sweep_adjoint_workspace_bytes(h, nsteps, ckpt_every) bytes,
+ * 256-byte aligned.  Asynchronous on the stream like the other runs.
+ */
+size_t sweep_adjoint_workspace_bytes(const sweep_t *h, int64_t nsteps, int ckpt_every);
+int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT, double *d_lam0,
+                  int64_t nsteps, int ckpt_every, void *d_ws, struct CUstream_st *stream);
 
 /*
  * Allocation-free form of sweep_run_swept (the paper has no counterpart;

@@ -1,0 +1,381 @@
+// adjoint.cuh -- discrete adjoints (reverse mode) of the two schemes.
+//
+// The swept rule only reorders the explicit scheme (Sec. 3.3), so the
+// gradient of a final-state loss L(Q^N) is the gradient of the step-by-step
+// scheme: lam^N = dL/dQ^N, lam^n = (dQ^{n+1}/dQ^n)^T lam^{n+1}.  Non-smooth
+// points (the limiter's switches, max of the wave speeds, |u_n|) take the
+// derivative of the branch the forward step took.
+//
+// Heat (App. A): the RK2 step Q' = Q + c2 L(Q + c1 L Q) has a symmetric L,
+// so its adjoint step is again a two-stage stencil update of radius 1,
+//   mu* = c2 t(lam),   lam_n = fma(c1, t(mu*), lam + mu*),
+// and runs through the swept kernels unchanged (equation type HeatAdj).
+//
+// Euler (App. B): per reverse step, with Q* = Q + lam1 d(Q) rebuilt from Q,
+//   mu*   = lam2 J(Q*)^T lam'
+//   lam_n = (lam' + mu*) + lam1 J(Q)^T mu*
+// where d(Q)_c = (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2} - Gh_{j+1/2}).  J^T v
+// is assembled face by face: each face's flux depends on the four cells of
+// its line, and its adjoint input is v_right - v_left; k_face_vjp writes the
+// four cells' contributions of every face and k_gather sums, per cell, the
+// contributions of its eight faces (x faces, then y faces, each in the order
+// of the face's index along its line, wrapped periodically).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace sweep {
+
+// ------------------------------------------------------------------ heat
+
+struct HeatAdj {
+    static constexpr int NC = 1;
+    static constexpr int N = 1;
+};
+
+template <int C>
+struct Stage<HeatAdj, C> {
+    __device__ static void run(const Params &p, Block<HeatAdj, C> &B, int64_t level, Rect R)
+    {
+        const bool second = (level & 1) == 0;
+        const double *src = B.buf[(level - 1) & 1];
+        const double *own = B.buf[level & 1];
+        const int wp = B.wp;
+        for_rect(band(R, B.rank, C), [&](int x, int y) {
+            const int i = y * wp + x;
+            const double s = __dadd_rn(__dadd_rn(src[i - 1], src[i + 1]),
+                                       __dadd_rn(src[i - wp], src[i + wp]));
+            const double t = __fma_rn(-4.0, src[i], s);
+            // first stage: mu* = r t(lam); second: fma(r/2, t(mu*), lam + mu*)
+            const double v = second ? __fma_rn(p.c1, t, __dadd_rn(own[i], src[i]))
+                                    : __dmul_rn(p.c2, t);
+            B.put(level, 0, i, v);
+        });
+    }
+};
+
+// ------------------------------------------------------------------ Euler
+
+// Half limiter factors of one cell (as limiter_halves) and, for the branch
+// taken, their derivatives with respect to dm and dp.  A factor that is a
+// quotient below 1 has derivative (1/den, -num/den^2) in (num, den); a
+// factor clipped to 1, or zero, has derivative 0.
+__device__ __forceinline__ void limiter_halves_grad(double dm, double dp, int mode, double &hp,
+                                                    double &hm, double &dhp_dm, double &dhp_dp,
+                                                    double &dhm_dm, double &dhm_dp)
+{
+    limiter_halves(dm, dp, mode, hp, hm);
+    dhp_dm = dhp_dp = dhm_dm = dhm_dp = 0.0;
+    if (mode == 2)
+        return;
+    const bool same = (dm > 0.0 && dp > 0.0) || (dm < 0.0 && dp < 0.0);
+    if (!same)
+        return;
+    // dm/dp and dp/dm, each used only where it is the factor and below 1
+    const double q_mp = __ddiv_rn(dm, dp);
+    const double q_pm = __ddiv_rn(dp, dm);
+    // textbook: plus = dm/dp, minus = dp/dm; printed orientation swaps them
+    const bool plus_is_mp = mode == 0;
+    double g_mp_dm = 0.0, g_mp_dp = 0.0, g_pm_dm = 0.0, g_pm_dp = 0.0;
+    if (q_mp < 1.0) {
+        g_mp_dm = __ddiv_rn(1.0, dp);
+        g_mp_dp = __ddiv_rn(-dm, __dmul_rn(dp, dp));
+    }
+    if (q_pm < 1.0) {
+        g_pm_dp = __ddiv_rn(1.0, dm);
+        g_pm_dm = __ddiv_rn(-dp, __dmul_rn(dm, dm));
+    }
+    // the halves carry a factor 1/2
+    dhp_dm = __dmul_rn(0.5, plus_is_mp ? g_mp_dm : g_pm_dm);
+    dhp_dp = __dmul_rn(0.5, plus_is_mp ? g_mp_dp : g_pm_dp);
+    dhm_dm = __dmul_rn(0.5, plus_is_mp ? g_pm_dm : g_mp_dm);
+    dhm_dp = __dmul_rn(0.5, plus_is_mp ? g_pm_dp : g_mp_dp);
+}
+
+// reverse of cell_pressure: add to qb the gradient of pb * P(q)
+__device__ __forceinline__ void cell_pressure_vjp(const double q[4], const EulerConst &k,
+                                                  double pb, double qb[4])
+{
+    const double inv = __drcp_rn(q[0]);
+    const double u = __dmul_rn(q[1], inv), v = __dmul_rn(q[2], inv);
+    const double eb = __dmul_rn(pb, k.gm1);
+    const double kb = __dmul_rn(__dmul_rn(-0.5, k.gm1), pb);
+    const double ub = __dmul_rn(kb, q[1]), vb = __dmul_rn(kb, q[2]);
+    const double mxb = __dadd_rn(__dmul_rn(kb, u), __dmul_rn(ub, inv));
+    const double myb = __dadd_rn(__dmul_rn(kb, v), __dmul_rn(vb, inv));
+    const double invb = __dadd_rn(__dmul_rn(ub, q[1]), __dmul_rn(vb, q[2]));
+    qb[0] = __dadd_rn(qb[0], __dmul_rn(__dmul_rn(-invb, inv), inv));
+    qb[1] = __dadd_rn(qb[1], mxb);
+    qb[2] = __dadd_rn(qb[2], myb);
+    qb[3] = __dadd_rn(qb[3], eb);
+}
+
+// reverse of state_flux (face-normal frame): add to qb the gradient of
+// <fb, F(q)> + lb * lam(q)
+__device__ __forceinline__ void state_flux_vjp(const double q[4], const EulerConst &k,
+                                               const double fb[4], double lb, double qb[4])
+{
+    const double inv = __drcp_rn(q[0]);
+    const double mn = q[1], mt = q[2], E = q[3];
+    const double un = __dmul_rn(mn, inv), ut = __dmul_rn(mt, inv);
+    const double ke2 = __fma_rn(mn, un, __dmul_rn(mt, ut));
+    const double p = __dmul_rn(k.gm1, __fma_rn(-0.5, ke2, E));
+    const double c = __dsqrt_rn(__dmul_rn(__dmul_rn(k.gamma, p), inv));
+    double mnb = fb[0], mtb, Eb, unb, utb, pb, invb;
+    // f1 = mn un + p
+    mnb = __dadd_rn(mnb, __dmul_rn(fb[1], un));
+    unb = __dmul_rn(fb[1], mn);
+    pb = fb[1];
+    // f2 = mt un
+    mtb = __dmul_rn(fb[2], un);
+    unb = __dadd_rn(unb, __dmul_rn(fb[2], mt));
+    // f3 = (E + p) un
+    Eb = __dmul_rn(fb[3], un);
+    pb = __dadd_rn(pb, __dmul_rn(fb[3], un));
+    unb = __dadd_rn(unb, __dmul_rn(fb[3], __dadd_rn(E, p)));
+    // lam = |un| + c
+    unb = __dadd_rn(unb, un > 0.0 ? lb : (un < 0.0 ? -lb : 0.0));
+    // c = sqrt(s), s = (gamma p) inv
+    const double sb = c > 0.0 ? __ddiv_rn(lb, __dmul_rn(2.0, c)) : 0.0;
+    pb = __dadd_rn(pb, __dmul_rn(__dmul_rn(sb, k.gamma), inv));
+    invb = __dmul_rn(__dmul_rn(sb, k.gamma), p);
+    // p = g1 (E - ke2/2)
+    Eb = __dadd_rn(Eb, __dmul_rn(pb, k.gm1));
+    const double kb = __dmul_rn(__dmul_rn(-0.5, k.gm1), pb);
+    // ke2 = mn un + mt ut
+    mnb = __dadd_rn(mnb, __dmul_rn(kb, un));
+    unb = __dadd_rn(unb, __dmul_rn(kb, mn));
+    mtb = __dadd_rn(mtb, __dmul_rn(kb, ut));
+    utb = __dmul_rn(kb, mt);
+    // un = mn inv, ut = mt inv
+    mnb = __dadd_rn(mnb, __dmul_rn(unb, inv));
+    invb = __dadd_rn(invb, __dmul_rn(unb, mn));
+    mtb = __dadd_rn(mtb, __dmul_rn(utb, inv));
+    invb = __dadd_rn(invb, __dmul_rn(utb, mt));
+    qb[0] = __dadd_rn(qb[0], __dmul_rn(__dmul_rn(-invb, inv), inv));
+    qb[1] = __dadd_rn(qb[1], mnb);
+    qb[2] = __dadd_rn(qb[2], mtb);
+    qb[3] = __dadd_rn(qb[3], Eb);
+}
+
+// Reverse of the numerical flux at the face between cells 1 and 2 of the
+// line of cells 0..3 (face-normal frame).  a: adjoint of the flux; qb[m]
+// receives the gradient for cell m (zeroed here).
+__device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double a[4],
+                                              const EulerConst &k, int mode, double qb[4][4])
+{
+    double p[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        p[m] = cell_pressure(q[m][0], q[m][1], q[m][2], q[m][3], k);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            qb[m][c] = 0.0;
+    }
+    double hl, hl_m, dl_dm, dl_dp, dl2, dl3;
+    double hr_p, hr, dr0, dr1, dr_dm, dr_dp;
+    // cell 1 towards its + face: (dm, dp) = (p1 - p0, p2 - p1)
+    limiter_halves_grad(__dadd_rn(p[1], -p[0]), __dadd_rn(p[2], -p[1]), mode, hl, hl_m, dl_dm,
+                        dl_dp, dl2, dl3);
+    // cell 2 towards its - face: (dm, dp) = (p2 - p1, p3 - p2)
+    limiter_halves_grad(__dadd_rn(p[2], -p[1]), __dadd_rn(p[3], -p[2]), mode, hr_p, hr, dr0, dr1,
+                        dr_dm, dr_dp);
+    double dq[4], ql[4], qr[4], fl[4], fr[4], laml, lamr;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        dq[c] = __dadd_rn(q[2][c], -q[1][c]);
+        ql[c] = __fma_rn(hl, dq[c], q[1][c]);
+        qr[c] = __fma_rn(-hr, dq[c], q[2][c]);
+    }
+    state_flux(ql[0], ql[1], ql[2], ql[3], k, fl, laml);
+    state_flux(qr[0], qr[1], qr[2], qr[3], k, fr, lamr);
+    const bool left = __double_as_longlong(laml) > __double_as_longlong(lamr);
+    const double r = left ? laml : lamr;
+    // Fh_c = 1/2 (r (ql_c - qr_c) + fl_c + fr_c)
+    double qlb[4], qrb[4], flb[4], frb[4], rb = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        flb[c] = __dmul_rn(0.5, a[c]);
+        frb[c] = flb[c];
+        qlb[c] = __dmul_rn(__dmul_rn(0.5, r), a[c]);
+        qrb[c] = __dmul_rn(__dmul_rn(-0.5, r), a[c]);
+        rb = __dadd_rn(rb, __dmul_rn(__dmul_rn(0.5, a[c]), __dadd_rn(ql[c], -qr[c])));
+    }
+    double sl[4] = {0.0, 0.0, 0.0, 0.0}, sr[4] = {0.0, 0.0, 0.0, 0.0};
+    state_flux_vjp(ql, k, flb, left ? rb : 0.0, sl);
+    state_flux_vjp(qr, k, frb, left ? 0.0 : rb, sr);
+    double hlb = 0.0, hrb = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        qlb[c] = __dadd_rn(qlb[c], sl[c]);
+        qrb[c] = __dadd_rn(qrb[c], sr[c]);
+        // ql = q1 + hl dq, qr = q2 - hr dq, dq = q2 - q1
+        const double dqb = __dadd_rn(__dmul_rn(qlb[c], hl), -__dmul_rn(qrb[c], hr));
+        hlb = __dadd_rn(hlb, __dmul_rn(qlb[c], dq[c]));
+        hrb = __dadd_rn(hrb, __dmul_rn(-qrb[c], dq[c]));
+        qb[1][c] = __dadd_rn(qb[1][c], __dadd_rn(qlb[c], -dqb));
+        qb[2][c] = __dadd_rn(qb[2][c], __dadd_rn(qrb[c], dqb));
+    }
+    // pressures: hl from (p1 - p0, p2 - p1), hr from (p2 - p1, p3 - p2)
+    double pb[4] = {0.0, 0.0, 0.0, 0.0};
+    const double a1 = __dmul_rn(hlb, dl_dm), a2 = __dmul_rn(hlb, dl_dp);
+    pb[1] = __dadd_rn(pb[1], a1);
+    pb[0] = __dadd_rn(pb[0], -a1);
+    pb[2] = __dadd_rn(pb[2], a2);
+    pb[1] = __dadd_rn(pb[1], -a2);
+    const double b1 = __dmul_rn(hrb, dr_dm), b2 = __dmul_rn(hrb, dr_dp);
+    pb[2] = __dadd_rn(pb[2], b1);
+    pb[1] = __dadd_rn(pb[1], -b1);
+    pb[3] = __dadd_rn(pb[3], b2);
+    pb[2] = __dadd_rn(pb[2], -b2);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        cell_pressure_vjp(q[m], k, pb[m], qb[m]);
+}
+
+// Rebuild the first stage: out = Q + lam1 d(Q) on every cell (tiles of
+// std_tile with a halo of n, like the Standard kernel's first stage).
+__global__ void __launch_bounds__(kThreads) k_stage1_euler(Params p, const double *q, double *out)
+{
+    extern __shared__ double smem[];
+    const int T = p.std_tile, n = Euler::N, wp = T + 2 * n;
+    Block<Euler, 1> B;
+    B.carve(smem, wp);
+    const int tx = (int)(p.nx / T);
+    const int I = blockIdx.x % tx, J = blockIdx.x / tx;
+    B.ox = (int64_t)I * T - n;
+    B.oy = (int64_t)J * T - n;
+    const int64_t gplane = p.nx * p.ny;
+    for_rect({0, wp, 0, wp}, [&](int x, int y) {
+        const int64_t g = gidx(p, B.ox, B.oy, x, y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            B.buf[0][c * B.plane + y * wp + x] = q[c * gplane + g];
+    });
+    __syncthreads();
+    Stage<Euler, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
+    __syncthreads();
+    for_rect({n, wp - n, n, wp - n}, [&](int x, int y) {
+        const int64_t g = gidx(p, B.ox, B.oy, x, y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            out[c * gplane + g] = B.buf[1][c * B.plane + y * wp + x];
+    });
+}
+
+// Per face (axis 0: between (i,j) and (i+1,j); axis 1: between (i,j) and
+// (i,j+1)): the contributions of <v_right - v_left, Fh(Q)> to the gradient of
+// the four cells of its line.  fo[(axis*16 + m*4 + c) * plane + j*nx + i],
+// cell m = 0..3 at offset m-1 along the axis, component c in the
+// (rho, m_x, m_y, E) order.
+__global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q, const double *v,
+                                                       double *fo)
+{
+    const int64_t plane = p.nx * p.ny;
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= 2 * plane)
+        return;
+    const int axis = (int)(f / plane);
+    const int64_t cell = f - axis * plane;
+    const int64_t i = cell % p.nx, j = cell / p.nx;
+    // normal-frame component order: (rho, m_n, m_t, E)
+    const int c1 = axis == 0 ? 1 : 2, c2 = axis == 0 ? 2 : 1;
+    double qq[4][4];
+    int64_t idx[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        int64_t ii = i, jj = j;
+        if (axis == 0) {
+            ii = i - 1 + m;
+            ii = ii < 0 ? ii + p.nx : (ii >= p.nx ? ii - p.nx : ii);
+        } else {
+            jj = j - 1 + m;
+            jj = jj < 0 ? jj + p.ny : (jj >= p.ny ? jj - p.ny : jj);
+        }
+        idx[m] = jj * p.nx + ii;
+        qq[m][0] = q[idx[m]];
+        qq[m][1] = q[c1 * plane + idx[m]];
+        qq[m][2] = q[c2 * plane + idx[m]];
+        qq[m][3] = q[3 * plane + idx[m]];
+    }
+    const double a[4] = {__dadd_rn(v[idx[2]], -v[idx[1]]),
+                         __dadd_rn(v[c1 * plane + idx[2]], -v[c1 * plane + idx[1]]),
+                         __dadd_rn(v[c2 * plane + idx[2]], -v[c2 * plane + idx[1]]),
+                         __dadd_rn(v[3 * plane + idx[2]], -v[3 * plane + idx[1]])};
+    double qb[4][4];
+    face_flux_vjp(qq, a, p.ek, p.literal, qb);
+    double *o = fo + (int64_t)axis * 16 * plane + cell;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        o[(m * 4 + 0) * plane] = qb[m][0];
+        o[(m * 4 + c1) * plane] = qb[m][1];
+        o[(m * 4 + c2) * plane] = qb[m][2];
+        o[(m * 4 + 3) * plane] = qb[m][3];
+    }
+}
+
+// Per cell: S = J^T v at the cell, summed from its eight faces in a fixed
+// order (x faces, then y faces; along each axis the faces in increasing
+// wrapped index), then
+//   mode 0:  mu = lam2 S                 (mu: out)
+//   mode 1:  lam = (lam + mu) + lam1 S   (lam: in place)
+__global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo, double *lam,
+                                                     double *mu, int mode)
+{
+    const int64_t plane = p.nx * p.ny;
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= plane)
+        return;
+    const int64_t i = cell % p.nx, j = cell / p.nx;
+    // the face at index e along an axis reaches this cell as its cell m with
+    // e = (pos + 1 - m) wrapped; visit the four faces in increasing e
+    int64_t ex[4], ey[4];
+    int mx[4], my[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        int64_t e = i + 1 - m;
+        ex[m] = e < 0 ? e + p.nx : (e >= p.nx ? e - p.nx : e);
+        e = j + 1 - m;
+        ey[m] = e < 0 ? e + p.ny : (e >= p.ny ? e - p.ny : e);
+        mx[m] = m;
+        my[m] = m;
+    }
+    // sort the four (e, m) pairs by e (insertion sort of four)
+#pragma unroll
+    for (int s = 1; s < 4; ++s)
+        for (int t = s; t > 0 && ex[t - 1] > ex[t]; --t) {
+            const int64_t te = ex[t];
+            ex[t] = ex[t - 1];
+            ex[t - 1] = te;
+            const int tm = mx[t];
+            mx[t] = mx[t - 1];
+            mx[t - 1] = tm;
+        }
+#pragma unroll
+    for (int s = 1; s < 4; ++s)
+        for (int t = s; t > 0 && ey[t - 1] > ey[t]; --t) {
+            const int64_t te = ey[t];
+            ey[t] = ey[t - 1];
+            ey[t - 1] = te;
+            const int tm = my[t];
+            my[t] = my[t - 1];
+            my[t - 1] = tm;
+        }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            s = __dadd_rn(s, fo[(int64_t)(0 * 16 + mx[t] * 4 + c) * plane + j * p.nx + ex[t]]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            s = __dadd_rn(s, fo[(int64_t)(1 * 16 + my[t] * 4 + c) * plane + ey[t] * p.nx + i]);
+        const int64_t o = c * plane + cell;
+        if (mode == 0)
+            mu[o] = __dmul_rn(p.c2, s);
+        else
+            lam[o] = __dadd_rn(__dadd_rn(lam[o], mu[o]), __dmul_rn(p.c1, s));
+    }
+}
+
+}  // namespace sweep

@@ -51,10 +51,18 @@ __device__ __forceinline__ double cell_pressure(double rho, double mx, double my
 // rounding is <= 1 and min() keeps it, while dp/dm > 1 rounds to >= 1 and
 // min() gives 1; symmetrically otherwise.  The sign and magnitude tests are
 // integer operations on the bit patterns, which keeps them off the FP64 pipe.
-// literal != 0 swaps the two factors (the orientation printed in App. B).
+// mode 1 swaps the two factors (the orientation printed in App. B); mode 2
+// applies no limiting (both factors 1: the face value is the two cells'
+// average), which is not a scheme of the paper and serves to check the
+// adjoint against finite differences where the scheme is smooth.
 __device__ __forceinline__ void limiter_halves(double dm, double dp, int literal, double &hp,
                                                double &hm)
 {
+    if (literal == 2) {
+        hp = 0.5;
+        hm = 0.5;
+        return;
+    }
     const unsigned long long bm = (unsigned long long)__double_as_longlong(dm);
     const unsigned long long bp = (unsigned long long)__double_as_longlong(dp);
     const unsigned long long am = bm & 0x7fffffffffffffffull;

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "sweep.h"
 
@@ -252,6 +253,94 @@ int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
     }
 }
 
+// ------------------------------------------------------------ adjoint
+
+struct AdjLayout {
+    size_t store, ckpt, seg, qs, mu, faces, total;  // byte offsets (after the header)
+    int64_t nseg, ckpt_every;
+};
+
+AdjLayout adjoint_layout(const sweep_s *h, int64_t nsteps, int64_t ckpt)
+{
+    AdjLayout L = {};
+    const size_t st = sizeof(double) * (size_t)slot_elems(h);
+    L.store = 0;
+    size_t off = st * (size_t)(h->depth + 1);  // level store of the swept forward
+    if (h->eqn == SWEEP_HEAT) {
+        L.total = off;
+        return L;
+    }
+    L.ckpt_every = ckpt;
+    L.nseg = nsteps > 0 ? (nsteps + ckpt - 1) / ckpt : 0;
+    L.ckpt = off;
+    off += st * (size_t)(L.nseg > 0 ? L.nseg : 1);
+    L.seg = off;
+    off += st * (size_t)ckpt;
+    L.qs = off;
+    off += st;
+    L.mu = off;
+    off += st;
+    L.faces = off;
+    off += sizeof(double) * 32 * (size_t)h->nx * (size_t)h->ny;
+    L.total = off;
+    return L;
+}
+
+int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0, int64_t nsteps,
+                  int64_t ckpt, void *ws, cudaStream_t st)
+{
+    const AdjLayout L = adjoint_layout(h, nsteps, ckpt);
+    char *base = (char *)ws + kHeader;
+    const size_t sbytes = sizeof(double) * 4 * (size_t)h->nx * (size_t)h->ny;
+    const size_t sstride = sizeof(double) * (size_t)slot_elems(h);
+    auto ckpt_ptr = [&](int64_t s) { return (double *)(base + L.ckpt + sstride * (size_t)s); };
+    auto seg_ptr = [&](int64_t t) { return (double *)(base + L.seg + sstride * (size_t)t); };
+    double *qs = (double *)(base + L.qs), *mu = (double *)(base + L.mu);
+    double *faces = (double *)(base + L.faces);
+    if (cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SWEEP_ECUDA;
+    if (nsteps == 0) return SWEEP_OK;
+    // forward pass: checkpoints every `ckpt` steps, advanced with the swept solver
+    if (cudaMemcpyAsync(ckpt_ptr(0), q0, sbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SWEEP_ECUDA;
+    for (int64_t s = 0; s + 1 < L.nseg; ++s) {
+        if (cudaMemcpyAsync(ckpt_ptr(s + 1), ckpt_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return SWEEP_ECUDA;
+        const int rc = swept<Euler>(h, make_params(h, ckpt_ptr(s + 1), ws), ckpt, st);
+        if (rc != SWEEP_OK) return rc;
+    }
+    // backward pass, segment by segment
+    Params p = make_params(h, nullptr, ws);
+    const int T = h->std_tile;
+    const size_t smem_std = smem_bytes<Euler>(T + 4 * Euler::N, 1);
+    const size_t smem_s1 = smem_bytes<Euler>(T + 2 * Euler::N, 1);
+    if (set_smem(k_standard<Euler>, smem_std) != cudaSuccess ||
+        set_smem(k_stage1_euler, smem_s1) != cudaSuccess)
+        return SWEEP_ECUDA;
+    const unsigned tiles = (unsigned)((h->nx / T) * (h->ny / T));
+    const int64_t plane = h->nx * h->ny;
+    const unsigned gf = (unsigned)((2 * plane + kThreads - 1) / kThreads);
+    const unsigned gc = (unsigned)((plane + kThreads - 1) / kThreads);
+    for (int64_t s = L.nseg - 1; s >= 0; --s) {
+        const int64_t len = (s + 1) * ckpt <= nsteps ? ckpt : nsteps - s * ckpt;
+        if (cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return SWEEP_ECUDA;
+        for (int64_t t = 0; t + 1 < len; ++t)
+            k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(p, seg_ptr(t), seg_ptr(t + 1));
+        for (int64_t t = len - 1; t >= 0; --t) {
+            k_stage1_euler<<<tiles, kThreads, smem_s1, st>>>(p, seg_ptr(t), qs);
+            k_face_vjp<<<gf, kThreads, 0, st>>>(p, qs, lam0, faces);
+            k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 0);
+            k_face_vjp<<<gf, kThreads, 0, st>>>(p, seg_ptr(t), mu, faces);
+            k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 1);
+        }
+        if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
+    }
+    return SWEEP_OK;
+}
+
 int check_run(const sweep_t *h, const double *state, int64_t nsteps, const void *ws)
 {
     if (!h || !state || !ws || nsteps < 0) return SWEEP_EINVAL;
@@ -326,7 +415,7 @@ SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
         if (!(std::isfinite(v) && v > 1.0)) return SWEEP_EINVAL;
         h->gamma = v;
     } else if (!std::strcmp(key, "limiter")) {
-        if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
+        if (v != 0.0 && v != 1.0 && v != 2.0) return SWEEP_EINVAL;
         h->limiter = (int)v;
     } else if (!std::strcmp(key, "scheme")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
@@ -403,6 +492,31 @@ SWEEP_API int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, vo
     const Params p = make_params(h, d_state, d_ws);
     if (h->eqn == SWEEP_HEAT) return standard_steps<Heat>(h, p, nsteps, stream);
     return standard_steps<Euler>(h, p, nsteps, stream);
+}
+
+SWEEP_API size_t sweep_adjoint_workspace_bytes(const sweep_t *h, int64_t nsteps, int ckpt_every)
+{
+    if (!h || nsteps < 0 || ckpt_every < 1) return 0;
+    return kHeader + adjoint_layout(h, nsteps, ckpt_every).total;
+}
+
+SWEEP_API int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT, double *d_lam0,
+                            int64_t nsteps, int ckpt_every, void *d_ws, CUstream_st *stream)
+{
+    if (!h || !d_lamT || !d_lam0 || !d_ws || nsteps < 0 || ckpt_every < 1) return SWEEP_EINVAL;
+    if (!aligned(d_lamT, 16) || !aligned(d_lam0, 16) || !aligned(d_ws, 256)) return SWEEP_EINVAL;
+    if (h->eqn == SWEEP_HEAT) {
+        if (h->scheme != 0) return SWEEP_EUNSUPPORTED;
+        const size_t bytes = sizeof(double) * (size_t)h->nx * (size_t)h->ny;
+        if (d_lam0 != d_lamT &&
+            cudaMemcpyAsync(d_lam0, d_lamT, bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+            return SWEEP_ECUDA;
+        // the heat step is linear with a symmetric stencil: its adjoint step
+        // is a two-stage stencil update of the same radius, run swept
+        return swept<HeatAdj>(h, make_params(h, d_lam0, d_ws), nsteps, stream);
+    }
+    if (!d_q0 || !aligned(d_q0, 16) || d_lam0 == d_lamT) return SWEEP_EINVAL;
+    return euler_adjoint(h, d_q0, d_lamT, d_lam0, nsteps, ckpt_every, d_ws, stream);
 }
 
 SWEEP_API int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds)

@@ -34,6 +34,8 @@ SIGNATURES = {
     "sweep_run_swept": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "sweep_run_standard": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "sweep_run_swept_static": (_c_int, [_vp, _vp, _c_i64, _vp]),
+    "sweep_adjoint_workspace_bytes": (ctypes.c_size_t, [_vp, _c_i64, _c_int]),
+    "sweep_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _c_i64, _c_int, _vp, _vp]),
     "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
     "sweep_destroy": (None, [_vp]),
     "sweep_error_string": (ctypes.c_char_p, [_c_int]),
@@ -109,6 +111,15 @@ def sweep_run_swept_static(h, state_ptr, nsteps, stream_ptr):
 
 
 STATIC_SCRATCH_BYTES = 16 << 20
+
+
+def sweep_adjoint_workspace_bytes(h, nsteps, ckpt_every):
+    return int(lib().sweep_adjoint_workspace_bytes(h, int(nsteps), int(ckpt_every)))
+
+
+def sweep_adjoint(h, q0_ptr, lamT_ptr, lam0_ptr, nsteps, ckpt_every, ws_ptr, stream_ptr):
+    return int(lib().sweep_adjoint(h, q0_ptr, lamT_ptr, lam0_ptr, int(nsteps), int(ckpt_every),
+                                   ws_ptr, stream_ptr))
 
 
 def sweep_profile_read(h, nkinds=5):
@@ -195,6 +206,24 @@ class Solver:
         """Advance `state` by nsteps with one kernel per RK2 step."""
         return self._run(sweep_run_standard, state, nsteps, ws)
 
+    def adjoint(self, q0, lamT, nsteps, ckpt_every=64):
+        """dL/dQ^0 given lamT = dL/dQ^N (device tensors of the state shape); returns a
+        new tensor.  q0 is the initial state (not read for heat)."""
+        import torch
+        if tuple(lamT.shape) != self._shape() or lamT.dtype != torch.float64 or not lamT.is_cuda:
+            raise ValueError("lamT must be a float64 CUDA tensor of shape %s" % (self._shape(),))
+        lamT = lamT.contiguous()
+        q0 = lamT if q0 is None else q0.contiguous()
+        lam0 = torch.empty_like(lamT)
+        nbytes = sweep_adjoint_workspace_bytes(self._h, nsteps, ckpt_every)
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=lamT.device)
+        stream = torch.cuda.current_stream(lamT.device).cuda_stream
+        rc = sweep_adjoint(self._h, ctypes.c_void_p(q0.data_ptr()), ctypes.c_void_p(lamT.data_ptr()),
+                           ctypes.c_void_p(lam0.data_ptr()), nsteps, ckpt_every,
+                           ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream))
+        _check(rc, "sweep_adjoint")
+        return lam0
+
     def profile(self):
         """{kind: (total ms, launches)} of the launches recorded since profiling was enabled."""
         ms, n = sweep_profile_read(self._h, len(KERNEL_KINDS))
@@ -210,3 +239,38 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class SweptRun(torch.autograd.Function):
+        """Q^N = swept(Q^0, nsteps); backward runs the discrete adjoint."""
+
+        @staticmethod
+        def forward(ctx, q0, solver, nsteps, ckpt_every):
+            ctx.solver, ctx.nsteps, ctx.ckpt = solver, int(nsteps), int(ckpt_every)
+            ctx.save_for_backward(q0)
+            q = q0.detach().clone().contiguous()
+            solver.run_swept(q, nsteps)
+            return q
+
+        @staticmethod
+        def backward(ctx, grad):
+            (q0,) = ctx.saved_tensors
+            g = ctx.solver.adjoint(q0.detach(), grad.contiguous(), ctx.nsteps, ctx.ckpt)
+            return g, None, None, None
+
+    return SweptRun
+
+
+_SweptRun = None
+
+
+def swept_run(q0, solver, nsteps, ckpt_every=64):
+    """Differentiable swept run: gradients of any loss of the result with
+    respect to q0 come from the discrete adjoint (sweep_adjoint)."""
+    global _SweptRun
+    if _SweptRun is None:
+        _SweptRun = _autograd_function()
+    return _SweptRun.apply(q0, solver, nsteps, ckpt_every)

@@ -63,7 +63,7 @@ def test_params_and_workspace(L):
     S.sweep_set_param(h, "gamma", 5.0 / 3.0)
     assert S.sweep_get_param(h, "gamma") == 5.0 / 3.0
     S.sweep_set_param(h, "limiter", 1)
-    for key, val in (("gamma", 1.0), ("limiter", 2), ("nope", 1.0), ("standard_tile", 7),
+    for key, val in (("gamma", 1.0), ("limiter", 3), ("nope", 1.0), ("standard_tile", 7),
                      ("standard_tile", 48)):
         with pytest.raises(S.SweepError):
             S.sweep_set_param(h, key, val)
@@ -84,3 +84,21 @@ def test_run_rejects_bad_pointers_before_any_launch(L):
         assert fn(h, ctypes.c_void_p(4096), -1, ctypes.c_void_p(4096), None) == S.SWEEP_EINVAL
     S.sweep_destroy(h)
     assert S.error_string(S.SWEEP_ETIMEOUT) == "device wait timed out"
+
+
+def test_adjoint_workspace_and_argument_checks(L):
+    h = S.sweep_create(S.SWEEP_EULER, 64, 64, 1e-3, 0.1, 32, 6)
+    slot = (4 * 64 * 64 * 8 + 255) // 256 * 256
+    # level store (7 slots) + 32 checkpoints + 64-step segment + Q* + mu* + faces
+    nseg = (2000 + 63) // 64
+    expect = 256 + slot * 7 + slot * nseg + slot * 64 + 2 * slot + 32 * 64 * 64 * 8
+    assert S.sweep_adjoint_workspace_bytes(h, 2000, 64) == expect
+    assert S.sweep_adjoint_workspace_bytes(h, 2000, 0) == 0
+    p = ctypes.c_void_p(4096)
+    assert S.sweep_adjoint(h, None, p, ctypes.c_void_p(8192), 5, 4, p, None) == S.SWEEP_EINVAL
+    assert S.sweep_adjoint(h, p, p, p, 5, 4, p, None) == S.SWEEP_EINVAL  # lam0 aliases lamT
+    assert S.sweep_adjoint(h, p, p, ctypes.c_void_p(8192), 5, 0, p, None) == S.SWEEP_EINVAL
+    S.sweep_destroy(h)
+    hh = S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)
+    assert S.sweep_adjoint_workspace_bytes(hh, 100, 64) == S.sweep_workspace_bytes(hh)
+    S.sweep_destroy(hh)
