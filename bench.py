@@ -10,7 +10,7 @@ resident in device memory; L2 is flushed (a 256 MiB write) between timed
 iterations.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload euler256|heat64|heat16384]
+                  [--workload euler256|heat64|heat16384|adjoint1024]
 
 --impl reference times the CPU oracle (the plain fp64 C reference) on the
 host cores on a bounded sample of the same workload.  Under torchrun
@@ -61,6 +61,16 @@ def workload(name):
         return dict(name="heat_modes_16384x16384_2000steps", eqn="heat", nx=16384, ny=16384,
                     dt=dt, dx=dx, nsteps=2000, tile=32, depth=14,
                     state=W.heat_modes(16384, 16384))
+    if name == "adjoint1024":
+        q0, dx = W.vortex(1024)
+        dt, _ = W.vortex_dt(q0, dx, 10.0, cfl=0.25)
+        target, _ = W.vortex(1024, beta=4.5, xc=0.5, yc=0.5)
+        # unlimited reconstruction: the minmod limiter's branch derivative is
+        # unbounded where the pressure is flat, and its exact discrete adjoint
+        # overflows long before 2000 steps
+        return dict(name="euler_vortex_1024x1024_2000steps_adjoint_ckpt64_unlimited", eqn="euler",
+                    nx=1024, ny=1024, dt=dt, dx=dx, nsteps=2000, tile=32, depth=6, state=q0,
+                    target=target[0], ckpt=64, adjoint=True, limiter=2)
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -186,6 +196,53 @@ def run_reference(args, wl):
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args, wl):
+    """Gradient of sum((rho_T - rho_target)^2) w.r.t. the initial state: one bench
+    step = one sweep_adjoint call (checkpointed swept forward pass + reverse
+    pass).  Reports Gcell-steps/s of the gradient and its time over the plain
+    swept forward run."""
+    import torch
+    from paper_2105_10332_b300 import sweep as S
+    dev = torch.device("cuda", torch.cuda.current_device())
+    solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"],
+                      limiter=wl.get("limiter", 0))
+    N, cells = wl["nsteps"], wl["nx"] * wl["ny"]
+    q0 = torch.from_numpy(wl["state"]).to(dev)
+    target = torch.from_numpy(wl["target"]).to(dev)
+    qN = q0.clone()
+    solver.run_swept(qN, N)
+    lamT = torch.zeros_like(q0)
+    lamT[0] = 2.0 * (qN[0] - target)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        solver.adjoint(q0, lamT, N, wl["ckpt"])
+    torch.cuda.synchronize(dev)
+    a0, a1 = ev(), ev()
+    a0.record()
+    for _ in range(args.steps):
+        g = solver.adjoint(q0, lamT, N, wl["ckpt"])
+    a1.record()
+    torch.cuda.synchronize(dev)
+    ms_adj = a0.elapsed_time(a1) / args.steps
+    f0, f1 = ev(), ev()
+    q = q0.clone()
+    f0.record()
+    solver.run_swept(q, N)
+    f1.record()
+    torch.cuda.synchronize(dev)
+    ms_fwd = f0.elapsed_time(f1)
+    line = {"metric": "Gcell-steps/s of the discrete adjoint (FP64, 1 B300)",
+            "value": round(cells * N / (ms_adj / 1e3) / 1e9, 6), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_adj, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded isentropic vortex)",
+            "config": {"workload": wl["name"], "nx": wl["nx"], "ny": wl["ny"], "steps_per_run": N,
+                       "ckpt_every": wl["ckpt"], "tile": wl["tile"], "depth": wl["depth"]},
+            "forward_ms": round(ms_fwd, 3), "adjoint_over_forward": round(ms_adj / ms_fwd, 3),
+            "grad_norm": float(torch.linalg.vector_norm(g))}
     print(json.dumps(line), flush=True)
 
 
@@ -345,6 +402,8 @@ def main():
     wl = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("adjoint"):
+        run_adjoint(args, wl)
     else:
         run_ours(args, wl)
 
