@@ -10,7 +10,7 @@ resident in device memory; L2 is flushed (a 256 MiB write) between timed
 iterations.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload euler256|heat64|heat16384|adjoint1024]
+                  [--workload euler256|heat64|heat16384|adjoint1024|batch256]
 
 --impl reference times the CPU oracle (the plain fp64 C reference) on the
 host cores on a bounded sample of the same workload.  Under torchrun
@@ -61,6 +61,9 @@ def workload(name):
         return dict(name="heat_modes_16384x16384_2000steps", eqn="heat", nx=16384, ny=16384,
                     dt=dt, dx=dx, nsteps=2000, tile=32, depth=14,
                     state=W.heat_modes(16384, 16384))
+    if name == "batch256":
+        return dict(name="batch_256_heat_euler_sides_64_2048_500steps", batch=True, count=256,
+                    nsteps=500)
     if name == "adjoint1024":
         q0, dx = W.vortex(1024)
         dt, _ = W.vortex_dt(q0, dx, 10.0, cfl=0.25)
@@ -196,6 +199,84 @@ def run_reference(args, wl):
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, wl):
+    """256 instances (even index heat, odd Euler vortex), square sides drawn
+    log-uniform in [64, 2048] (multiples of 32, seeded), 500 steps each, knobs
+    from the autotuner per (equation, size class).  One bench step = one
+    replay of the captured batch graph; the baseline runs each instance alone,
+    one after another."""
+    import torch
+    from paper_2105_10332_b300 import autotune, sweep as S, workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sides = W.batch_sides(wl["count"])
+    tuner = autotune.Autotuner()
+    solvers, init, cells = [], [], 0
+    for k, n in enumerate(sides):
+        if k % 2 == 0:
+            dt, dx = W.heat_dt(n, 0.1)
+            u0 = W.heat_modes(n, n, seed=20210521 + k)
+            eqn = "heat"
+        else:
+            u0, dx = W.vortex(n)
+            dt, _ = W.vortex_dt(u0, dx, 10.0)
+            eqn = "euler"
+        t = torch.from_numpy(u0).to(dev)
+        cfg = dict(tuner.best(eqn, n, dt, dx, t))
+        tile, depth = cfg.pop("tile"), cfg.pop("depth")
+        solvers.append(S.Solver(eqn, n, n, dt, dx, tile, depth, **cfg))
+        init.append(t)
+        cells += n * n
+    N = wl["nsteps"]
+    states = [t.clone() for t in init]
+    # each instance alone, one after another
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    solo_ms = 0.0
+    for s_, st, t in zip(solvers, states, init):
+        st.copy_(t)
+        s_.run_swept(st, N)  # warm-up of this instance's kernels
+        st.copy_(t)
+        torch.cuda.synchronize(dev)
+        a, b = ev(), ev()
+        a.record()
+        s_.run_swept(st, N)
+        b.record()
+        torch.cuda.synchronize(dev)
+        solo_ms += a.elapsed_time(b)
+    solo_out = [st.clone() for st in states]
+    batch = S.Batch(solvers, states, N)
+    batch.capture()
+    for _ in range(max(args.warmup, 1)):
+        for st, t in zip(states, init):
+            st.copy_(t)
+        batch.replay()
+    torch.cuda.synchronize(dev)
+    ms = 0.0
+    for _ in range(args.steps):
+        for st, t in zip(states, init):
+            st.copy_(t)
+        torch.cuda.synchronize(dev)
+        a, b = ev(), ev()
+        a.record()
+        batch.replay()
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms += a.elapsed_time(b)
+    ms /= args.steps
+    identical = all(torch.equal(x, y) for x, y in zip(states, solo_out))
+    classes = sorted(set((k[0], k[1]) for k in tuner.cache))
+    line = {"metric": "aggregate Gcell-steps/s, batched (one graph launch) vs each instance alone",
+            "value": round(cells * N / (ms / 1e3) / 1e9, 6), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded heat modes / isentropic vortices)",
+            "config": {"workload": wl["name"], "instances": len(sides), "steps_per_instance": N,
+                       "cells_total": cells},
+            "solo": {"value": round(cells * N / (solo_ms / 1e3) / 1e9, 6), "ms": round(solo_ms, 3)},
+            "batched_over_solo": round(solo_ms / ms, 4), "bit_identical_to_solo": identical,
+            "autotuned": {"%s/%d" % c: tuner.cache[c] for c in classes}}
     print(json.dumps(line), flush=True)
 
 
@@ -404,6 +485,8 @@ def main():
         run_reference(args, wl)
     elif wl.get("adjoint"):
         run_adjoint(args, wl)
+    elif wl.get("batch"):
+        run_batch(args, wl)
     else:
         run_ours(args, wl)
 

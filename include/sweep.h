@@ -159,6 +159,23 @@ int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT, double *
                   int64_t nsteps, int ckpt_every, void *d_ws, struct CUstream_st *stream);
 
 /*
+ * Batched swept runs: advance d_states[i] (device, each in its instance's
+ * layout) in place by nsteps[i] with handle hs[i], for i < count.  The
+ * instances are independent and may differ in equation, size, tile, depth
+ * and cluster settings.  Each instance's launch sequence goes to one of a
+ * pool of internal streams (largest work first), forked from `stream` and
+ * joined back into it by events: the instances overlap on the GPU and the
+ * whole batch can be captured from `stream` into one CUDA graph.  The first
+ * call on a device creates the stream pool (make it before any capture).
+ * d_ws: sweep_batch_workspace_bytes(hs, count) bytes, 256-byte aligned,
+ * carved into one region per instance.  Each result is bit-identical to
+ * that instance's sweep_run_swept.  A handle must appear once per batch.
+ */
+size_t sweep_batch_workspace_bytes(sweep_t *const *hs, int count);
+int sweep_batch_run(sweep_t *const *hs, double *const *d_states, const int64_t *nsteps, int count,
+                    void *d_ws, struct CUstream_st *stream);
+
+/*
  * Allocation-free form of sweep_run_swept (the paper has no counterpart;
  * this is an interface convenience).
  *

@@ -519,6 +519,102 @@ SWEEP_API int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT
     return euler_adjoint(h, d_q0, d_lamT, d_lam0, nsteps, ckpt_every, d_ws, stream);
 }
 
+// ------------------------------------------------------------------ batch
+//
+// A batch runs every instance's swept launch sequence on one of a pool of
+// internal streams, forked from and joined back into the caller's stream by
+// events, so that independent instances overlap on the GPU and the whole
+// batch can be captured from the caller's stream into one CUDA graph.
+
+namespace {
+constexpr int kBatchStreams = 16;
+constexpr int kMaxBatchDevices = 64;
+std::mutex batch_mu;
+struct BatchPool {
+    cudaStream_t s[kBatchStreams];
+    cudaEvent_t done[kBatchStreams];
+    cudaEvent_t fork;
+    bool ready;
+};
+BatchPool batch_pool[kMaxBatchDevices];
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+SWEEP_API size_t sweep_batch_workspace_bytes(sweep_t *const *hs, int count)
+{
+    if (!hs || count < 0) return 0;
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i]) return 0;
+        total += align256(sweep_workspace_bytes(hs[i]));
+    }
+    return total;
+}
+
+SWEEP_API int sweep_batch_run(sweep_t *const *hs, double *const *d_states, const int64_t *nsteps,
+                              int count, void *d_ws, CUstream_st *stream)
+{
+    if (!hs || !d_states || !nsteps || count < 0 || (count > 0 && !d_ws)) return SWEEP_EINVAL;
+    if (!aligned(d_ws, 256)) return SWEEP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i] || !d_states[i] || nsteps[i] < 0 || !aligned(d_states[i], 16)) return SWEEP_EINVAL;
+        if (hs[i]->eqn == SWEEP_HEAT && hs[i]->scheme != 0) return SWEEP_EUNSUPPORTED;
+    }
+    if (count == 0) return SWEEP_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxBatchDevices) return SWEEP_ECUDA;
+    BatchPool *bp = &batch_pool[dev];
+    {
+        std::lock_guard<std::mutex> lock(batch_mu);
+        if (!bp->ready) {
+            for (int k = 0; k < kBatchStreams; ++k)
+                if (cudaStreamCreateWithFlags(&bp->s[k], cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&bp->done[k], cudaEventDisableTiming) != cudaSuccess)
+                    return SWEEP_ECUDA;
+            if (cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) != cudaSuccess)
+                return SWEEP_ECUDA;
+            bp->ready = true;
+        }
+    }
+    // largest work first, dealt round-robin over the streams
+    std::vector<int> order(count);
+    std::vector<double> cost(count);
+    for (int i = 0; i < count; ++i) {
+        order[i] = i;
+        cost[i] = (double)hs[i]->nx * (double)hs[i]->ny * (double)nsteps[i] *
+                  (hs[i]->eqn == SWEEP_HEAT ? 1.0 : 50.0);
+    }
+    for (int a = 1; a < count; ++a)
+        for (int b = a; b > 0 && cost[order[b - 1]] < cost[order[b]]; --b) {
+            const int t = order[b];
+            order[b] = order[b - 1];
+            order[b - 1] = t;
+        }
+    std::vector<size_t> off(count);
+    size_t o = 0;
+    for (int i = 0; i < count; ++i) {
+        off[i] = o;
+        o += align256(sweep_workspace_bytes(hs[i]));
+    }
+    const int ns = count < kBatchStreams ? count : kBatchStreams;
+    if (cudaEventRecord(bp->fork, stream) != cudaSuccess) return SWEEP_ECUDA;
+    for (int k = 0; k < ns; ++k)
+        if (cudaStreamWaitEvent(bp->s[k], bp->fork, 0) != cudaSuccess) return SWEEP_ECUDA;
+    int rc = SWEEP_OK;
+    for (int r = 0; r < count && rc == SWEEP_OK; ++r) {
+        const int i = order[r];
+        rc = sweep_run_swept(hs[i], d_states[i], nsteps[i], (char *)d_ws + off[i], bp->s[r % ns]);
+    }
+    // join every stream back, even after an error, so no stream is left forked
+    for (int k = 0; k < ns; ++k) {
+        if (cudaEventRecord(bp->done[k], bp->s[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(stream, bp->done[k], 0) != cudaSuccess)
+            rc = rc == SWEEP_OK ? SWEEP_ECUDA : rc;
+    }
+    return rc;
+}
+
 SWEEP_API int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds)
 {
     if (!h || !ms || !launches || nkinds <= 0) return SWEEP_EINVAL;

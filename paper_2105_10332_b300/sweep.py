@@ -35,6 +35,9 @@ SIGNATURES = {
     "sweep_run_standard": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "sweep_run_swept_static": (_c_int, [_vp, _vp, _c_i64, _vp]),
     "sweep_adjoint_workspace_bytes": (ctypes.c_size_t, [_vp, _c_i64, _c_int]),
+    "sweep_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(_vp), _c_int]),
+    "sweep_batch_run": (_c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_c_i64),
+                                 _c_int, _vp, _vp]),
     "sweep_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _c_i64, _c_int, _vp, _vp]),
     "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
     "sweep_destroy": (None, [_vp]),
@@ -239,6 +242,60 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def sweep_batch_workspace_bytes(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    return int(lib().sweep_batch_workspace_bytes(arr, len(handles)))
+
+
+def sweep_batch_run(handles, state_ptrs, nsteps, ws_ptr, stream_ptr):
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    ps = (ctypes.c_void_p * n)(*state_ptrs)
+    ns = (ctypes.c_int64 * n)(*[int(x) for x in nsteps])
+    return int(lib().sweep_batch_run(hs, ps, ns, n, ws_ptr, stream_ptr))
+
+
+class Batch:
+    """Many independent solvers advanced together (sweep_batch_run), optionally
+    captured once into a CUDA graph and replayed."""
+
+    def __init__(self, solvers, states, nsteps):
+        import torch
+        self.solvers = list(solvers)
+        self.states = list(states)
+        self.nsteps = [int(n) for n in (nsteps if hasattr(nsteps, "__len__") else
+                                          [nsteps] * len(self.solvers))]
+        for s, st in zip(self.solvers, self.states):
+            if tuple(st.shape) != s._shape() or st.dtype != torch.float64 or not st.is_cuda:
+                raise ValueError("each state must be a float64 CUDA tensor of its solver's shape")
+        self._handles = [s._h for s in self.solvers]
+        nbytes = sweep_batch_workspace_bytes(self._handles)
+        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.states[0].device)
+        self.graph = None
+
+    def _launch(self, stream):
+        rc = sweep_batch_run(self._handles, [t.data_ptr() for t in self.states], self.nsteps,
+                             ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_void_p(stream))
+        _check(rc, "sweep_batch_run")
+
+    def run(self):
+        import torch
+        self._launch(torch.cuda.current_stream(self.states[0].device).cuda_stream)
+
+    def capture(self):
+        """Record one batch into a CUDA graph (replay() then runs it with one launch)."""
+        import torch
+        self.run()  # first call creates the stream pool and sets kernel attributes
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._launch(torch.cuda.current_stream().cuda_stream)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
 
 
 def _autograd_function():

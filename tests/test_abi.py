@@ -102,3 +102,25 @@ def test_adjoint_workspace_and_argument_checks(L):
     hh = S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)
     assert S.sweep_adjoint_workspace_bytes(hh, 100, 64) == S.sweep_workspace_bytes(hh)
     S.sweep_destroy(hh)
+
+
+def test_autotune_candidates_are_legal():
+    from paper_2105_10332_b300 import autotune
+    for eqn in ("heat", "euler"):
+        for side in (64, 96, 160, 512, 2048):
+            c = autotune.candidates(eqn, side)
+            assert c, (eqn, side)
+            for cfg in c:
+                assert side % cfg["tile"] == 0 and side // cfg["tile"] >= 2
+                n = 1 if eqn == "heat" else 2
+                assert 2 <= cfg["depth"] <= cfg["tile"] // (2 * n) - 1 and cfg["depth"] % 2 == 0
+    assert autotune.size_class(96) == 128 and autotune.size_class(64) == 64
+
+
+def test_batch_workspace_is_sum_of_instances(L):
+    hs = [S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6),
+          S.sweep_create(S.SWEEP_EULER, 96, 96, 1e-3, 0.1, 32, 6)]
+    total = sum((S.sweep_workspace_bytes(h) + 255) // 256 * 256 for h in hs)
+    assert S.sweep_batch_workspace_bytes(hs) == total
+    for h in hs:
+        S.sweep_destroy(h)
