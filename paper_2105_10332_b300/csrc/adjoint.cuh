@@ -233,36 +233,6 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
         cell_pressure_vjp(q[m], k, pb[m], qb[m]);
 }
 
-// Rebuild the first stage: out = Q + lam1 d(Q) on every cell (tiles of
-// std_tile with a halo of n, like the Standard kernel's first stage).
-__global__ void __launch_bounds__(kThreads) k_stage1_euler(Params p, const double *q, double *out)
-{
-    extern __shared__ double smem[];
-    const int T = p.std_tile, n = Euler::N, wp = T + 2 * n;
-    Block<Euler, 1> B;
-    B.carve(smem, wp);
-    const int tx = (int)(p.nx / T);
-    const int I = blockIdx.x % tx, J = blockIdx.x / tx;
-    B.ox = (int64_t)I * T - n;
-    B.oy = (int64_t)J * T - n;
-    const int64_t gplane = p.nx * p.ny;
-    for_rect({0, wp, 0, wp}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            B.buf[0][c * B.plane + y * wp + x] = q[c * gplane + g];
-    });
-    __syncthreads();
-    Stage<Euler, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
-    __syncthreads();
-    for_rect({n, wp - n, n, wp - n}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            out[c * gplane + g] = B.buf[1][c * B.plane + y * wp + x];
-    });
-}
-
 // Per face (axis 0: between (i,j) and (i+1,j); axis 1: between (i,j) and
 // (i,j+1)): the contributions of <v_right - v_left, Fh(Q)> to the gradient of
 // the four cells of its line.  fo[(axis*16 + m*4 + c) * plane + j*nx + i],

@@ -140,21 +140,34 @@ struct Bracket {
     }
 };
 
-// Standard steps: ping-pong between the state and slot 0 of the workspace,
-// ending in the state.
+// Standard launches over `nlevels` levels: two levels (one RK2 step, or two
+// forward-Euler steps) per launch and, for an odd count, one single-level
+// launch; ping-pong between the state and slot 0 of the workspace, ending in
+// the state.
 template <class EQ>
-int standard_steps(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
-    if (nsteps <= 0) return SWEEP_OK;
+    if (nlevels <= 0) return SWEEP_OK;
     const int T = h->std_tile;
     const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N, 1);
-    if (set_smem(k_standard<EQ>, smem) != cudaSuccess) return SWEEP_ECUDA;
+    const size_t smem1 = smem_bytes<EQ>(T + 2 * EQ::N, 1);
+    if (set_smem(k_standard<EQ>, smem) != cudaSuccess || set_smem(k_level1<EQ>, smem1) != cudaSuccess)
+        return SWEEP_ECUDA;
     const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
     double *a = p.state, *b = p.ws;
-    for (int64_t s = 0; s < nsteps; ++s) {
+    for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
             k_standard<EQ><<<grid, kThreads, smem, st>>>(p, a, b);
+        }
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (nlevels & 1) {
+        {
+            Bracket br(h, st, kKindStandard);
+            k_level1<EQ><<<grid, kThreads, smem1, st>>>(p, a, b);
         }
         double *t = a;
         a = b;
@@ -195,9 +208,9 @@ cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, size_t smem, cudaS
 }
 
 template <class EQ, int C, int CB>
-int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
-    const int64_t L = 2 * nsteps;
+    const int64_t L = nlevels;
     const int d = h->depth;
     int64_t done = 0;
     if (L >= d) {
@@ -230,27 +243,44 @@ int swept_c(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
         if (e != cudaSuccess) return SWEEP_ECUDA;
         done = (m + 1) * d;
     }
-    return standard_steps<EQ>(h, p, (L - done) / 2, st);
+    return standard_levels<EQ>(h, p, L - done, st);
 }
 
 template <class EQ, int C>
-int swept_b(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+int swept_b(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
     switch (h->cluster_br) {
-    case 2: return swept_c<EQ, C, 2>(h, p, nsteps, st);
-    case 4: return swept_c<EQ, C, 4>(h, p, nsteps, st);
-    default: return swept_c<EQ, C, 1>(h, p, nsteps, st);
+    case 2: return swept_c<EQ, C, 2>(h, p, nlevels, st);
+    case 4: return swept_c<EQ, C, 4>(h, p, nlevels, st);
+    default: return swept_c<EQ, C, 1>(h, p, nlevels, st);
     }
 }
 
+// swept run over `nlevels` stage-levels (2 per RK2 step, 1 per forward-Euler step)
 template <class EQ>
-int swept(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+int swept(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
     switch (h->cluster) {
-    case 2: return swept_b<EQ, 2>(h, p, nsteps, st);
-    case 4: return swept_b<EQ, 4>(h, p, nsteps, st);
-    default: return swept_b<EQ, 1>(h, p, nsteps, st);
+    case 2: return swept_b<EQ, 2>(h, p, nlevels, st);
+    case 4: return swept_b<EQ, 4>(h, p, nlevels, st);
+    default: return swept_b<EQ, 1>(h, p, nlevels, st);
     }
+}
+
+bool heat_fe(const sweep_s *h) { return h->eqn == SWEEP_HEAT && h->scheme == 1; }
+
+int run_swept_any(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    if (heat_fe(h)) return swept<HeatFE>(h, p, nsteps, st);
+    if (h->eqn == SWEEP_HEAT) return swept<Heat>(h, p, 2 * nsteps, st);
+    return swept<Euler>(h, p, 2 * nsteps, st);
+}
+
+int run_standard_any(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st)
+{
+    if (heat_fe(h)) return standard_levels<HeatFE>(h, p, nsteps, st);
+    if (h->eqn == SWEEP_HEAT) return standard_levels<Heat>(h, p, 2 * nsteps, st);
+    return standard_levels<Euler>(h, p, 2 * nsteps, st);
 }
 
 // ------------------------------------------------------------ adjoint
@@ -307,7 +337,7 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
         if (cudaMemcpyAsync(ckpt_ptr(s + 1), ckpt_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess)
             return SWEEP_ECUDA;
-        const int rc = swept<Euler>(h, make_params(h, ckpt_ptr(s + 1), ws), ckpt, st);
+        const int rc = swept<Euler>(h, make_params(h, ckpt_ptr(s + 1), ws), 2 * ckpt, st);
         if (rc != SWEEP_OK) return rc;
     }
     // backward pass, segment by segment
@@ -316,7 +346,7 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
     const size_t smem_std = smem_bytes<Euler>(T + 4 * Euler::N, 1);
     const size_t smem_s1 = smem_bytes<Euler>(T + 2 * Euler::N, 1);
     if (set_smem(k_standard<Euler>, smem_std) != cudaSuccess ||
-        set_smem(k_stage1_euler, smem_s1) != cudaSuccess)
+        set_smem(k_level1<Euler>, smem_s1) != cudaSuccess)
         return SWEEP_ECUDA;
     const unsigned tiles = (unsigned)((h->nx / T) * (h->ny / T));
     const int64_t plane = h->nx * h->ny;
@@ -330,7 +360,7 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
         for (int64_t t = 0; t + 1 < len; ++t)
             k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(p, seg_ptr(t), seg_ptr(t + 1));
         for (int64_t t = len - 1; t >= 0; --t) {
-            k_stage1_euler<<<tiles, kThreads, smem_s1, st>>>(p, seg_ptr(t), qs);
+            k_level1<Euler><<<tiles, kThreads, smem_s1, st>>>(p, seg_ptr(t), qs);
             k_face_vjp<<<gf, kThreads, 0, st>>>(p, qs, lam0, faces);
             k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 0);
             k_face_vjp<<<gf, kThreads, 0, st>>>(p, seg_ptr(t), mu, faces);
@@ -345,7 +375,6 @@ int check_run(const sweep_t *h, const double *state, int64_t nsteps, const void 
 {
     if (!h || !state || !ws || nsteps < 0) return SWEEP_EINVAL;
     if (!aligned(state, 16) || !aligned(ws, 256)) return SWEEP_EINVAL;
-    if (h->eqn == SWEEP_HEAT && h->scheme != 0) return SWEEP_EUNSUPPORTED;
     return SWEEP_OK;
 }
 
@@ -479,9 +508,7 @@ SWEEP_API int sweep_run_swept(sweep_t *h, double *d_state, int64_t nsteps, void 
 {
     const int rc = check_run(h, d_state, nsteps, d_ws);
     if (rc != SWEEP_OK) return rc;
-    const Params p = make_params(h, d_state, d_ws);
-    if (h->eqn == SWEEP_HEAT) return swept<Heat>(h, p, nsteps, stream);
-    return swept<Euler>(h, p, nsteps, stream);
+    return run_swept_any(h, make_params(h, d_state, d_ws), nsteps, stream);
 }
 
 SWEEP_API int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
@@ -489,9 +516,7 @@ SWEEP_API int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, vo
 {
     const int rc = check_run(h, d_state, nsteps, d_ws);
     if (rc != SWEEP_OK) return rc;
-    const Params p = make_params(h, d_state, d_ws);
-    if (h->eqn == SWEEP_HEAT) return standard_steps<Heat>(h, p, nsteps, stream);
-    return standard_steps<Euler>(h, p, nsteps, stream);
+    return run_standard_any(h, make_params(h, d_state, d_ws), nsteps, stream);
 }
 
 SWEEP_API size_t sweep_adjoint_workspace_bytes(const sweep_t *h, int64_t nsteps, int ckpt_every)
@@ -506,14 +531,15 @@ SWEEP_API int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT
     if (!h || !d_lamT || !d_lam0 || !d_ws || nsteps < 0 || ckpt_every < 1) return SWEEP_EINVAL;
     if (!aligned(d_lamT, 16) || !aligned(d_lam0, 16) || !aligned(d_ws, 256)) return SWEEP_EINVAL;
     if (h->eqn == SWEEP_HEAT) {
-        if (h->scheme != 0) return SWEEP_EUNSUPPORTED;
         const size_t bytes = sizeof(double) * (size_t)h->nx * (size_t)h->ny;
         if (d_lam0 != d_lamT &&
             cudaMemcpyAsync(d_lam0, d_lamT, bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
             return SWEEP_ECUDA;
         // the heat step is linear with a symmetric stencil: its adjoint step
-        // is a two-stage stencil update of the same radius, run swept
-        return swept<HeatAdj>(h, make_params(h, d_lam0, d_ws), nsteps, stream);
+        // is a stencil update of the same radius, run swept (the
+        // forward-Euler step is its own adjoint)
+        if (heat_fe(h)) return swept<HeatFE>(h, make_params(h, d_lam0, d_ws), nsteps, stream);
+        return swept<HeatAdj>(h, make_params(h, d_lam0, d_ws), 2 * nsteps, stream);
     }
     if (!d_q0 || !aligned(d_q0, 16) || d_lam0 == d_lamT) return SWEEP_EINVAL;
     return euler_adjoint(h, d_q0, d_lamT, d_lam0, nsteps, ckpt_every, d_ws, stream);
@@ -559,7 +585,6 @@ SWEEP_API int sweep_batch_run(sweep_t *const *hs, double *const *d_states, const
     if (!aligned(d_ws, 256)) return SWEEP_EINVAL;
     for (int i = 0; i < count; ++i) {
         if (!hs[i] || !d_states[i] || nsteps[i] < 0 || !aligned(d_states[i], 16)) return SWEEP_EINVAL;
-        if (hs[i]->eqn == SWEEP_HEAT && hs[i]->scheme != 0) return SWEEP_EUNSUPPORTED;
     }
     if (count == 0) return SWEEP_OK;
     int dev = -1;

@@ -110,7 +110,7 @@ def vortex(nx, ny=None, beta=5.0, gamma=1.4, u_inf=1.0, v_inf=1.0, rho_inf=1.0, 
     return np.ascontiguousarray(q), dx
 
 
-def vortex_table_a1(nx, ny=None, gamma=1.4, half_width=5.0):
+def vortex_table_a1(nx, ny=None, gamma=1.4, half_width=5.0, xc=0.0, yc=0.0):
     """Vortex with the constants of App. B, Table A1 (alpha = 45 deg, M = sqrt(2/gamma),
     beta = M 5 sqrt(2)/(4 pi) e^{1/2}, R = sigma = 1, p_inf = 1/gamma normalisation).
 
@@ -125,6 +125,8 @@ def vortex_table_a1(nx, ny=None, gamma=1.4, half_width=5.0):
     xs = -L + (np.arange(nx) + 0.5) * dx
     ys = -L + (np.arange(ny) + 0.5) * (2 * L / ny)
     X, Y = np.meshgrid(xs, ys)
+    X = (X - xc + L) % (2 * L) - L
+    Y = (Y - yc + L) % (2 * L) - L
     M = math.sqrt(2.0 / gamma)
     beta = M * 5.0 * math.sqrt(2.0) / (4.0 * math.pi) * math.exp(0.5)
     om = beta * np.exp(-0.5 * (X * X + Y * Y))
