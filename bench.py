@@ -10,7 +10,7 @@ resident in device memory; L2 is flushed (a 256 MiB write) between timed
 iterations.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload euler256|heat64|heat16384|adjoint1024|batch256]
+                  [--workload euler256|heat64|heat4096|heat16384|adjoint1024|batch256]
 
 --impl reference times the CPU oracle (the plain fp64 C reference) on the
 host cores on a bounded sample of the same workload.  Under torchrun
@@ -56,6 +56,11 @@ def workload(name):
         dt, dx = W.heat_dt(64, 0.1)
         return dict(name="heat_sine_64x64_500steps", eqn="heat", nx=64, ny=64, dt=dt, dx=dx,
                     nsteps=500, tile=16, depth=6, state=W.heat_sine(64, 64))
+    if name == "heat4096":
+        # a profiling-size heat case: state 128 MiB (larger than L2), level store 4 GiB
+        dt, dx = W.heat_dt(4096, 0.1)
+        return dict(name="heat_modes_4096x4096_200steps", eqn="heat", nx=4096, ny=4096, dt=dt,
+                    dx=dx, nsteps=200, tile=64, depth=30, state=W.heat_modes(4096, 4096))
     if name == "heat16384":
         dt, dx = W.heat_dt(16384, 0.1)
         return dict(name="heat_modes_16384x16384_2000steps", eqn="heat", nx=16384, ny=16384,
