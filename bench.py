@@ -42,7 +42,8 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands (profiles/); an entry is removed whenever that kernel changes.
-TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9249024 + 0}
+TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9281280 + 0,
+                      ("heat_modes_4096x4096_200steps", "octahedron"): 1518874 + 445693952}
 
 
 def workload(name):
