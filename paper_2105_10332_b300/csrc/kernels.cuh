@@ -233,18 +233,26 @@ __device__ __forceinline__ void for_diff(Rect O, Rect I, F &&f)
     const int a2 = a1 + wl * hi;
     const int total = a2 + wr * hi;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        // the branches pick coordinates only: f has one call site, so a warp
+        // whose lanes fall in different parts still runs its body once
+        int x, y;
         if (q < a0) {
-            f(O.x0 + q % wo, O.y0 + q / wo);
+            x = O.x0 + q % wo;
+            y = O.y0 + q / wo;
         } else if (q < a1) {
             const int r = q - a0;
-            f(O.x0 + r % wo, I.y1 + r / wo);
+            x = O.x0 + r % wo;
+            y = I.y1 + r / wo;
         } else if (q < a2) {
             const int r = q - a1;
-            f(O.x0 + r % wl, I.y0 + r / wl);
+            x = O.x0 + r % wl;
+            y = I.y0 + r / wl;
         } else {
             const int r = q - a2;
-            f(I.x1 + r % wr, I.y0 + r / wr);
+            x = I.x1 + r % wr;
+            y = I.y0 + r / wr;
         }
+        f(x, y);
     }
 }
 
@@ -369,20 +377,35 @@ struct Stage<Euler, C> {
         const int py0 = ya - 2;  // P rows [ya-2, yb+2)
         const int hy0 = ya - 1;  // HY rows [ya-1, yb+1)
 
-        // (a) cell pressures: S's rows +-2 in x, and 2 rows above and below S
+        // Each phase below walks one index space over all its items, and the
+        // branches on the index pick addresses only: the FP64 body has a
+        // single call site, so a warp that straddles two parts of the space
+        // does not run it once per part (every FP64 warp instruction costs
+        // the same issue time however few of its lanes are active).
+        //
+        // (a) cell pressures: 2 rows below S and 2 above (S's columns), then
+        //     S's rows widened by 2 on each side
         if (!idle) {
-            const Rect rx = {S.x0 - 2, S.x1 + 2, S.y0, S.y1};
-            const Rect ry = {S.x0, S.x1, S.y0 - 2, S.y1 + 2};
-            for_diff(ry, S, [&](int x, int y) {
+            const int W = S.w(), band2 = 2 * W, wide = W + 4;
+            const int total = 2 * band2 + wide * S.h();
+            for (int q = threadIdx.x; q < total; q += blockDim.x) {
+                int x, y;
+                if (q < band2) {
+                    x = S.x0 + q % W;
+                    y = S.y0 - 2 + q / W;
+                } else if (q < 2 * band2) {
+                    const int r = q - band2;
+                    x = S.x0 + r % W;
+                    y = S.y1 + r / W;
+                } else {
+                    const int r = q - 2 * band2;
+                    x = S.x0 - 2 + r % wide;
+                    y = S.y0 + r / wide;
+                }
                 const int i = y * wp + x;
                 B.P[(y - py0) * wp + x] =
                     cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
-            });
-            for_rect(rx, [&](int x, int y) {
-                const int i = y * wp + x;
-                B.P[(y - py0) * wp + x] =
-                    cell_pressure(src[i], src[pl + i], src[2 * pl + i], src[3 * pl + i], k);
-            });
+            }
         }
         __syncthreads();
         // (b) half limiter factors: x on [x0-1, x1+1) x S.rows, y on S.cols x [ya-1, yb+1)
@@ -391,27 +414,34 @@ struct Stage<Euler, C> {
             const Rect ly = {S.x0, S.x1, S.y0 - 1, S.y1 + 1};
             const int nlx = lx.area(), total = nlx + ly.area();
             for (int q = threadIdx.x; q < total; q += blockDim.x) {
+                int j, st;
+                double *hp, *hm;
                 if (q < nlx) {
                     const int x = lx.x0 + q % lx.w(), y = lx.y0 + q / lx.w();
-                    const int j = (y - py0) * wp + x;
-                    const double pc = B.P[j];
+                    j = (y - py0) * wp + x;
+                    st = 1;
                     const int o = (y - ya) * wp + x;
-                    limiter_halves(__dadd_rn(pc, -B.P[j - 1]), __dadd_rn(B.P[j + 1], -pc),
-                                   p.literal, B.hxp[o], B.hxm[o]);
+                    hp = B.hxp + o;
+                    hm = B.hxm + o;
                 } else {
                     const int r = q - nlx;
                     const int x = ly.x0 + r % ly.w(), y = ly.y0 + r / ly.w();
-                    const int j = (y - py0) * wp + x;
-                    const double pc = B.P[j];
+                    j = (y - py0) * wp + x;
+                    st = wp;
                     const int o = (y - hy0) * wp + x;
-                    limiter_halves(__dadd_rn(pc, -B.P[j - wp]), __dadd_rn(B.P[j + wp], -pc),
-                                   p.literal, B.hyp[o], B.hym[o]);
+                    hp = B.hyp + o;
+                    hm = B.hym + o;
                 }
+                const double pc = B.P[j];
+                limiter_halves(__dadd_rn(pc, -B.P[j - st]), __dadd_rn(B.P[j + st], -pc), p.literal,
+                               *hp, *hm);
             }
         }
         __syncthreads();
         // (c) face fluxes: x faces f = x0..x1 on S's rows (between f-1 and f),
-        //     y faces g = ya..yb on S's columns (between g-1 and g)
+        //     y faces g = ya..yb on S's columns (between g-1 and g); a y face
+        //     takes its states in the y-normal frame (rho, m_y, m_x, E), that
+        //     is components 2 and 1 swapped on the way in and on the way out
         const int W = S.w(), Hh = S.h();
         const int fxw = W + 1;
         const int nfx = fxw * Hh;
@@ -422,35 +452,44 @@ struct Stage<Euler, C> {
         if (!idle) {
             const int total = nfx + nfy;
             for (int q = threadIdx.x; q < total; q += blockDim.x) {
-                double fh[4];
+                int i0, st, ca, cb, opl;
+                const double *hl, *hr;
+                double *out;
                 if (q < nfx) {
                     const int fo = q % fxw, yo = q / fxw;
                     const int x = S.x0 + fo, y = S.y0 + yo;
-                    const int i0 = y * wp + x - 1, i1 = i0 + 1;
-                    const double q0[4] = {src[i0], src[pl + i0], src[2 * pl + i0], src[3 * pl + i0]};
-                    const double q1[4] = {src[i1], src[pl + i1], src[2 * pl + i1], src[3 * pl + i1]};
+                    i0 = y * wp + x - 1;
+                    st = 1;
+                    ca = 1;
+                    cb = 2;
                     const int h0 = yo * wp + x - 1;
-                    face_flux(q0, q1, B.hxp[h0], B.hxm[h0 + 1], k, fh);
-                    const int o = yo * fxw + fo;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        B.fx[c * fxpl + o] = fh[c];
+                    hl = B.hxp + h0;
+                    hr = B.hxm + h0 + 1;
+                    out = B.fx + yo * fxw + fo;
+                    opl = fxpl;
                 } else {
                     const int r = q - nfx;
                     const int xo = r % W, go = r / W;
                     const int x = S.x0 + xo, y = S.y0 + go;
-                    const int i0 = (y - 1) * wp + x, i1 = i0 + wp;
-                    // y-normal frame: (rho, m_y, m_x, E)
-                    const double q0[4] = {src[i0], src[2 * pl + i0], src[pl + i0], src[3 * pl + i0]};
-                    const double q1[4] = {src[i1], src[2 * pl + i1], src[pl + i1], src[3 * pl + i1]};
+                    i0 = (y - 1) * wp + x;
+                    st = wp;
+                    ca = 2;
+                    cb = 1;
                     const int h0 = (y - 1 - hy0) * wp + x;
-                    face_flux(q0, q1, B.hyp[h0], B.hym[h0 + wp], k, fh);
-                    const int o = go * W + xo;
-                    B.fy[o] = fh[0];
-                    B.fy[fypl + o] = fh[2];
-                    B.fy[2 * fypl + o] = fh[1];
-                    B.fy[3 * fypl + o] = fh[3];
+                    hl = B.hyp + h0;
+                    hr = B.hym + h0 + wp;
+                    out = B.fy + go * W + xo;
+                    opl = fypl;
                 }
+                const int i1 = i0 + st;
+                const double q0[4] = {src[i0], src[ca * pl + i0], src[cb * pl + i0], src[3 * pl + i0]};
+                const double q1[4] = {src[i1], src[ca * pl + i1], src[cb * pl + i1], src[3 * pl + i1]};
+                double fh[4];
+                face_flux(q0, q1, *hl, *hr, k, fh);
+                out[0] = fh[0];
+                out[ca * opl] = fh[1];
+                out[cb * opl] = fh[2];
+                out[3 * opl] = fh[3];
             }
         }
         __syncthreads();
