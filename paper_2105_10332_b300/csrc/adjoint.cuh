@@ -41,14 +41,14 @@ struct Stage<HeatAdj, C> {
         const double *src = B.buf[(level - 1) & 1];
         const double *own = B.buf[level & 1];
         const int wp = B.wp;
+        const Fx F = p.ek.f;
         for_rect(band(R, B.rank, C), [&](int x, int y) {
             const int i = y * wp + x;
-            const double s = __dadd_rn(__dadd_rn(src[i - 1], src[i + 1]),
-                                       __dadd_rn(src[i - wp], src[i + wp]));
+            const double s = fadd(fadd(src[i - 1], src[i + 1], F), fadd(src[i - wp], src[i + wp], F), F);
             const double t = __fma_rn(-4.0, src[i], s);
             // first stage: mu* = r t(lam); second: fma(r/2, t(mu*), lam + mu*)
-            const double v = second ? __fma_rn(p.c1, t, __dadd_rn(own[i], src[i]))
-                                    : __dmul_rn(p.c2, t);
+            const double v = second ? __fma_rn(p.c1, t, fadd(own[i], src[i], F))
+                                    : fmul(p.c2, t, F);
             B.put(level, 0, i, v);
         });
     }
@@ -60,11 +60,11 @@ struct Stage<HeatAdj, C> {
 // taken, their derivatives with respect to dm and dp.  A factor that is a
 // quotient below 1 has derivative (1/den, -num/den^2) in (num, den); a
 // factor clipped to 1, or zero, has derivative 0.
-__device__ __forceinline__ void limiter_halves_grad(double dm, double dp, int mode, double &hp,
-                                                    double &hm, double &dhp_dm, double &dhp_dp,
-                                                    double &dhm_dm, double &dhm_dp)
+__device__ __forceinline__ void limiter_halves_grad(double dm, double dp, int mode, const Fx &F,
+                                                    double &hp, double &hm, double &dhp_dm,
+                                                    double &dhp_dp, double &dhm_dm, double &dhm_dp)
 {
-    limiter_halves(dm, dp, mode, hp, hm);
+    limiter_halves(dm, dp, mode, F, hp, hm);
     dhp_dm = dhp_dp = dhm_dm = dhm_dp = 0.0;
     if (mode == 2)
         return;
@@ -79,35 +79,36 @@ __device__ __forceinline__ void limiter_halves_grad(double dm, double dp, int mo
     double g_mp_dm = 0.0, g_mp_dp = 0.0, g_pm_dm = 0.0, g_pm_dp = 0.0;
     if (q_mp < 1.0) {
         g_mp_dm = __ddiv_rn(1.0, dp);
-        g_mp_dp = __ddiv_rn(-dm, __dmul_rn(dp, dp));
+        g_mp_dp = __ddiv_rn(-dm, fmul(dp, dp, F));
     }
     if (q_pm < 1.0) {
         g_pm_dp = __ddiv_rn(1.0, dm);
-        g_pm_dm = __ddiv_rn(-dp, __dmul_rn(dm, dm));
+        g_pm_dm = __ddiv_rn(-dp, fmul(dm, dm, F));
     }
     // the halves carry a factor 1/2
-    dhp_dm = __dmul_rn(0.5, plus_is_mp ? g_mp_dm : g_pm_dm);
-    dhp_dp = __dmul_rn(0.5, plus_is_mp ? g_mp_dp : g_pm_dp);
-    dhm_dm = __dmul_rn(0.5, plus_is_mp ? g_pm_dm : g_mp_dm);
-    dhm_dp = __dmul_rn(0.5, plus_is_mp ? g_pm_dp : g_mp_dp);
+    dhp_dm = fmul(0.5, plus_is_mp ? g_mp_dm : g_pm_dm, F);
+    dhp_dp = fmul(0.5, plus_is_mp ? g_mp_dp : g_pm_dp, F);
+    dhm_dm = fmul(0.5, plus_is_mp ? g_pm_dm : g_mp_dm, F);
+    dhm_dp = fmul(0.5, plus_is_mp ? g_pm_dp : g_mp_dp, F);
 }
 
 // reverse of cell_pressure: add to qb the gradient of pb * P(q)
 __device__ __forceinline__ void cell_pressure_vjp(const double q[4], const EulerConst &k,
                                                   double pb, double qb[4])
 {
+    const Fx &F = k.f;
     const double inv = __drcp_rn(q[0]);
-    const double u = __dmul_rn(q[1], inv), v = __dmul_rn(q[2], inv);
-    const double eb = __dmul_rn(pb, k.gm1);
-    const double kb = __dmul_rn(__dmul_rn(-0.5, k.gm1), pb);
-    const double ub = __dmul_rn(kb, q[1]), vb = __dmul_rn(kb, q[2]);
-    const double mxb = __dadd_rn(__dmul_rn(kb, u), __dmul_rn(ub, inv));
-    const double myb = __dadd_rn(__dmul_rn(kb, v), __dmul_rn(vb, inv));
-    const double invb = __dadd_rn(__dmul_rn(ub, q[1]), __dmul_rn(vb, q[2]));
-    qb[0] = __dadd_rn(qb[0], __dmul_rn(__dmul_rn(-invb, inv), inv));
-    qb[1] = __dadd_rn(qb[1], mxb);
-    qb[2] = __dadd_rn(qb[2], myb);
-    qb[3] = __dadd_rn(qb[3], eb);
+    const double u = fmul(q[1], inv, F), v = fmul(q[2], inv, F);
+    const double eb = fmul(pb, k.gm1, F);
+    const double kb = fmul(fmul(-0.5, k.gm1, F), pb, F);
+    const double ub = fmul(kb, q[1], F), vb = fmul(kb, q[2], F);
+    const double mxb = fadd(fmul(kb, u, F), fmul(ub, inv, F), F);
+    const double myb = fadd(fmul(kb, v, F), fmul(vb, inv, F), F);
+    const double invb = fadd(fmul(ub, q[1], F), fmul(vb, q[2], F), F);
+    qb[0] = fadd(qb[0], fmul(fmul(-invb, inv, F), inv, F), F);
+    qb[1] = fadd(qb[1], mxb, F);
+    qb[2] = fadd(qb[2], myb, F);
+    qb[3] = fadd(qb[3], eb, F);
 }
 
 // reverse of state_flux (face-normal frame): add to qb the gradient of
@@ -115,47 +116,48 @@ __device__ __forceinline__ void cell_pressure_vjp(const double q[4], const Euler
 __device__ __forceinline__ void state_flux_vjp(const double q[4], const EulerConst &k,
                                                const double fb[4], double lb, double qb[4])
 {
+    const Fx &F = k.f;
     const double inv = __drcp_rn(q[0]);
     const double mn = q[1], mt = q[2], E = q[3];
-    const double un = __dmul_rn(mn, inv), ut = __dmul_rn(mt, inv);
-    const double ke2 = __fma_rn(mn, un, __dmul_rn(mt, ut));
-    const double p = __dmul_rn(k.gm1, __fma_rn(-0.5, ke2, E));
-    const double c = __dsqrt_rn(__dmul_rn(__dmul_rn(k.gamma, p), inv));
+    const double un = fmul(mn, inv, F), ut = fmul(mt, inv, F);
+    const double ke2 = __fma_rn(mn, un, fmul(mt, ut, F));
+    const double p = fmul(k.gm1, __fma_rn(-0.5, ke2, E), F);
+    const double c = __dsqrt_rn(fmul(fmul(k.gamma, p, F), inv, F));
     double mnb = fb[0], mtb, Eb, unb, utb, pb, invb;
     // f1 = mn un + p
-    mnb = __dadd_rn(mnb, __dmul_rn(fb[1], un));
-    unb = __dmul_rn(fb[1], mn);
+    mnb = fadd(mnb, fmul(fb[1], un, F), F);
+    unb = fmul(fb[1], mn, F);
     pb = fb[1];
     // f2 = mt un
-    mtb = __dmul_rn(fb[2], un);
-    unb = __dadd_rn(unb, __dmul_rn(fb[2], mt));
+    mtb = fmul(fb[2], un, F);
+    unb = fadd(unb, fmul(fb[2], mt, F), F);
     // f3 = (E + p) un
-    Eb = __dmul_rn(fb[3], un);
-    pb = __dadd_rn(pb, __dmul_rn(fb[3], un));
-    unb = __dadd_rn(unb, __dmul_rn(fb[3], __dadd_rn(E, p)));
+    Eb = fmul(fb[3], un, F);
+    pb = fadd(pb, fmul(fb[3], un, F), F);
+    unb = fadd(unb, fmul(fb[3], fadd(E, p, F), F), F);
     // lam = |un| + c
-    unb = __dadd_rn(unb, un > 0.0 ? lb : (un < 0.0 ? -lb : 0.0));
+    unb = fadd(unb, un > 0.0 ? lb : (un < 0.0 ? -lb : 0.0), F);
     // c = sqrt(s), s = (gamma p) inv
-    const double sb = c > 0.0 ? __ddiv_rn(lb, __dmul_rn(2.0, c)) : 0.0;
-    pb = __dadd_rn(pb, __dmul_rn(__dmul_rn(sb, k.gamma), inv));
-    invb = __dmul_rn(__dmul_rn(sb, k.gamma), p);
+    const double sb = c > 0.0 ? __ddiv_rn(lb, fmul(2.0, c, F)) : 0.0;
+    pb = fadd(pb, fmul(fmul(sb, k.gamma, F), inv, F), F);
+    invb = fmul(fmul(sb, k.gamma, F), p, F);
     // p = g1 (E - ke2/2)
-    Eb = __dadd_rn(Eb, __dmul_rn(pb, k.gm1));
-    const double kb = __dmul_rn(__dmul_rn(-0.5, k.gm1), pb);
+    Eb = fadd(Eb, fmul(pb, k.gm1, F), F);
+    const double kb = fmul(fmul(-0.5, k.gm1, F), pb, F);
     // ke2 = mn un + mt ut
-    mnb = __dadd_rn(mnb, __dmul_rn(kb, un));
-    unb = __dadd_rn(unb, __dmul_rn(kb, mn));
-    mtb = __dadd_rn(mtb, __dmul_rn(kb, ut));
-    utb = __dmul_rn(kb, mt);
+    mnb = fadd(mnb, fmul(kb, un, F), F);
+    unb = fadd(unb, fmul(kb, mn, F), F);
+    mtb = fadd(mtb, fmul(kb, ut, F), F);
+    utb = fmul(kb, mt, F);
     // un = mn inv, ut = mt inv
-    mnb = __dadd_rn(mnb, __dmul_rn(unb, inv));
-    invb = __dadd_rn(invb, __dmul_rn(unb, mn));
-    mtb = __dadd_rn(mtb, __dmul_rn(utb, inv));
-    invb = __dadd_rn(invb, __dmul_rn(utb, mt));
-    qb[0] = __dadd_rn(qb[0], __dmul_rn(__dmul_rn(-invb, inv), inv));
-    qb[1] = __dadd_rn(qb[1], mnb);
-    qb[2] = __dadd_rn(qb[2], mtb);
-    qb[3] = __dadd_rn(qb[3], Eb);
+    mnb = fadd(mnb, fmul(unb, inv, F), F);
+    invb = fadd(invb, fmul(unb, mn, F), F);
+    mtb = fadd(mtb, fmul(utb, inv, F), F);
+    invb = fadd(invb, fmul(utb, mt, F), F);
+    qb[0] = fadd(qb[0], fmul(fmul(-invb, inv, F), inv, F), F);
+    qb[1] = fadd(qb[1], mnb, F);
+    qb[2] = fadd(qb[2], mtb, F);
+    qb[3] = fadd(qb[3], Eb, F);
 }
 
 // Reverse of the numerical flux at the face between cells 1 and 2 of the
@@ -164,6 +166,7 @@ __device__ __forceinline__ void state_flux_vjp(const double q[4], const EulerCon
 __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double a[4],
                                               const EulerConst &k, int mode, double qb[4][4])
 {
+    const Fx &F = k.f;
     double p[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -175,15 +178,15 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
     double hl, hl_m, dl_dm, dl_dp, dl2, dl3;
     double hr_p, hr, dr0, dr1, dr_dm, dr_dp;
     // cell 1 towards its + face: (dm, dp) = (p1 - p0, p2 - p1)
-    limiter_halves_grad(__dadd_rn(p[1], -p[0]), __dadd_rn(p[2], -p[1]), mode, hl, hl_m, dl_dm,
+    limiter_halves_grad(fadd(p[1], -p[0], F), fadd(p[2], -p[1], F), mode, F, hl, hl_m, dl_dm,
                         dl_dp, dl2, dl3);
     // cell 2 towards its - face: (dm, dp) = (p2 - p1, p3 - p2)
-    limiter_halves_grad(__dadd_rn(p[2], -p[1]), __dadd_rn(p[3], -p[2]), mode, hr_p, hr, dr0, dr1,
+    limiter_halves_grad(fadd(p[2], -p[1], F), fadd(p[3], -p[2], F), mode, F, hr_p, hr, dr0, dr1,
                         dr_dm, dr_dp);
     double dq[4], ql[4], qr[4], fl[4], fr[4], laml, lamr;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        dq[c] = __dadd_rn(q[2][c], -q[1][c]);
+        dq[c] = fadd(q[2][c], -q[1][c], F);
         ql[c] = __fma_rn(hl, dq[c], q[1][c]);
         qr[c] = __fma_rn(-hr, dq[c], q[2][c]);
     }
@@ -195,11 +198,11 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
     double qlb[4], qrb[4], flb[4], frb[4], rb = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        flb[c] = __dmul_rn(0.5, a[c]);
+        flb[c] = fmul(0.5, a[c], F);
         frb[c] = flb[c];
-        qlb[c] = __dmul_rn(__dmul_rn(0.5, r), a[c]);
-        qrb[c] = __dmul_rn(__dmul_rn(-0.5, r), a[c]);
-        rb = __dadd_rn(rb, __dmul_rn(__dmul_rn(0.5, a[c]), __dadd_rn(ql[c], -qr[c])));
+        qlb[c] = fmul(fmul(0.5, r, F), a[c], F);
+        qrb[c] = fmul(fmul(-0.5, r, F), a[c], F);
+        rb = fadd(rb, fmul(fmul(0.5, a[c], F), fadd(ql[c], -qr[c], F), F), F);
     }
     double sl[4] = {0.0, 0.0, 0.0, 0.0}, sr[4] = {0.0, 0.0, 0.0, 0.0};
     state_flux_vjp(ql, k, flb, left ? rb : 0.0, sl);
@@ -207,27 +210,27 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
     double hlb = 0.0, hrb = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        qlb[c] = __dadd_rn(qlb[c], sl[c]);
-        qrb[c] = __dadd_rn(qrb[c], sr[c]);
+        qlb[c] = fadd(qlb[c], sl[c], F);
+        qrb[c] = fadd(qrb[c], sr[c], F);
         // ql = q1 + hl dq, qr = q2 - hr dq, dq = q2 - q1
-        const double dqb = __dadd_rn(__dmul_rn(qlb[c], hl), -__dmul_rn(qrb[c], hr));
-        hlb = __dadd_rn(hlb, __dmul_rn(qlb[c], dq[c]));
-        hrb = __dadd_rn(hrb, __dmul_rn(-qrb[c], dq[c]));
-        qb[1][c] = __dadd_rn(qb[1][c], __dadd_rn(qlb[c], -dqb));
-        qb[2][c] = __dadd_rn(qb[2][c], __dadd_rn(qrb[c], dqb));
+        const double dqb = fadd(fmul(qlb[c], hl, F), -fmul(qrb[c], hr, F), F);
+        hlb = fadd(hlb, fmul(qlb[c], dq[c], F), F);
+        hrb = fadd(hrb, fmul(-qrb[c], dq[c], F), F);
+        qb[1][c] = fadd(qb[1][c], fadd(qlb[c], -dqb, F), F);
+        qb[2][c] = fadd(qb[2][c], fadd(qrb[c], dqb, F), F);
     }
     // pressures: hl from (p1 - p0, p2 - p1), hr from (p2 - p1, p3 - p2)
     double pb[4] = {0.0, 0.0, 0.0, 0.0};
-    const double a1 = __dmul_rn(hlb, dl_dm), a2 = __dmul_rn(hlb, dl_dp);
-    pb[1] = __dadd_rn(pb[1], a1);
-    pb[0] = __dadd_rn(pb[0], -a1);
-    pb[2] = __dadd_rn(pb[2], a2);
-    pb[1] = __dadd_rn(pb[1], -a2);
-    const double b1 = __dmul_rn(hrb, dr_dm), b2 = __dmul_rn(hrb, dr_dp);
-    pb[2] = __dadd_rn(pb[2], b1);
-    pb[1] = __dadd_rn(pb[1], -b1);
-    pb[3] = __dadd_rn(pb[3], b2);
-    pb[2] = __dadd_rn(pb[2], -b2);
+    const double a1 = fmul(hlb, dl_dm, F), a2 = fmul(hlb, dl_dp, F);
+    pb[1] = fadd(pb[1], a1, F);
+    pb[0] = fadd(pb[0], -a1, F);
+    pb[2] = fadd(pb[2], a2, F);
+    pb[1] = fadd(pb[1], -a2, F);
+    const double b1 = fmul(hrb, dr_dm, F), b2 = fmul(hrb, dr_dp, F);
+    pb[2] = fadd(pb[2], b1, F);
+    pb[1] = fadd(pb[1], -b1, F);
+    pb[3] = fadd(pb[3], b2, F);
+    pb[2] = fadd(pb[2], -b2, F);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
         cell_pressure_vjp(q[m], k, pb[m], qb[m]);
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q
                                                        double *fo)
 {
     const int64_t plane = p.nx * p.ny;
+    const Fx F = p.ek.f;
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= 2 * plane)
         return;
@@ -268,10 +272,10 @@ __global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q
         qq[m][2] = q[c2 * plane + idx[m]];
         qq[m][3] = q[3 * plane + idx[m]];
     }
-    const double a[4] = {__dadd_rn(v[idx[2]], -v[idx[1]]),
-                         __dadd_rn(v[c1 * plane + idx[2]], -v[c1 * plane + idx[1]]),
-                         __dadd_rn(v[c2 * plane + idx[2]], -v[c2 * plane + idx[1]]),
-                         __dadd_rn(v[3 * plane + idx[2]], -v[3 * plane + idx[1]])};
+    const double a[4] = {fadd(v[idx[2]], -v[idx[1]], F),
+                         fadd(v[c1 * plane + idx[2]], -v[c1 * plane + idx[1]], F),
+                         fadd(v[c2 * plane + idx[2]], -v[c2 * plane + idx[1]], F),
+                         fadd(v[3 * plane + idx[2]], -v[3 * plane + idx[1]], F)};
     double qb[4][4];
     face_flux_vjp(qq, a, p.ek, p.literal, qb);
     double *o = fo + (int64_t)axis * 16 * plane + cell;
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo,
                                                      double *mu, int mode)
 {
     const int64_t plane = p.nx * p.ny;
+    const Fx F = p.ek.f;
     const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= plane)
         return;
@@ -336,15 +341,15 @@ __global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo,
         double s = 0.0;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-            s = __dadd_rn(s, fo[(int64_t)(0 * 16 + mx[t] * 4 + c) * plane + j * p.nx + ex[t]]);
+            s = fadd(s, fo[(int64_t)(0 * 16 + mx[t] * 4 + c) * plane + j * p.nx + ex[t]], F);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-            s = __dadd_rn(s, fo[(int64_t)(1 * 16 + my[t] * 4 + c) * plane + ey[t] * p.nx + i]);
+            s = fadd(s, fo[(int64_t)(1 * 16 + my[t] * 4 + c) * plane + ey[t] * p.nx + i], F);
         const int64_t o = c * plane + cell;
         if (mode == 0)
-            mu[o] = __dmul_rn(p.c2, s);
+            mu[o] = fmul(p.c2, s, F);
         else
-            lam[o] = __dadd_rn(__dadd_rn(lam[o], mu[o]), __dmul_rn(p.c1, s));
+            lam[o] = fadd(fadd(lam[o], mu[o], F), fmul(p.c1, s, F), F);
     }
 }
 

@@ -334,7 +334,8 @@ struct Stage<Heat, C> {
         for_rect(band(R, B.rank, C), [&](int x, int y) {
             const int i = y * wp + x;
             B.put(level, 0, i,
-                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c));
+                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c,
+                              p.ek.f));
         });
     }
 };
@@ -348,7 +349,8 @@ struct Stage<HeatFE, C> {
         for_rect(band(R, B.rank, C), [&](int x, int y) {
             const int i = y * wp + x;
             B.put(level, 0, i,
-                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], src[i], p.c2));
+                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], src[i], p.c2,
+                              p.ek.f));
         });
     }
 };
@@ -433,8 +435,8 @@ struct Stage<Euler, C> {
                     hm = B.hym + o;
                 }
                 const double pc = B.P[j];
-                limiter_halves(__dadd_rn(pc, -B.P[j - st]), __dadd_rn(B.P[j + st], -pc), p.literal,
-                               *hp, *hm);
+                limiter_halves(fadd(pc, -B.P[j - st], k.f), fadd(B.P[j + st], -pc, k.f), p.literal,
+                               k.f, *hp, *hm);
             }
         }
         __syncthreads();
@@ -505,7 +507,7 @@ struct Stage<Euler, C> {
                     B.put(level, c, i,
                           euler_combine(B.fx[c * fxpl + ofx], B.fx[c * fxpl + ofx + 1],
                                         B.fy[c * fypl + ofy], B.fy[c * fypl + ofy + W],
-                                        own[c * pl + i], lam));
+                                        own[c * pl + i], lam, k.f));
             });
         }
     }

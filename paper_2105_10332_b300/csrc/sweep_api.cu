@@ -92,6 +92,8 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     }
     p.ek.gamma = h->gamma;
     p.ek.gm1 = h->gamma - 1.0;
+    p.ek.f.one = 1.0;
+    p.ek.f.nzero = -0.0;
     p.literal = h->limiter;
     p.state = state;
     p.ws = ws ? (double *)((char *)ws + kHeader) : nullptr;
