@@ -41,9 +41,12 @@ FLOPS_PER_CELL_STAGE = {"heat": 7, "euler": 187}
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (profiles/); an entry is removed whenever that kernel changes.
-TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9281280 + 0,
-                      ("heat_modes_4096x4096_200steps", "octahedron"): 1518874 + 445693952}
+# stands (profiles/); an entry is removed whenever that kernel changes.  The
+# 16384^2 heat Octahedron has none: at 4096^2 its reads of the Bridges'
+# exports hit L2 (1.5 of 448 MB), at 16384^2 the exports (16x) cannot, so the
+# smaller capture does not scale in proportion.
+TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9246720 + 0,
+                      ("heat_modes_4096x4096_200steps", "octahedron"): 1519754 + 445980672}
 
 
 def workload(name):
