@@ -149,8 +149,10 @@ int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
  *          d_lam0 may equal d_lamT.
  *   Euler: a forward swept pass from d_q0 keeps a checkpoint every
  *          ckpt_every steps; each segment is then recomputed one Standard
- *          step at a time and reversed step by step (face-wise reverse mode
- *          of the flux, gathered per cell).  d_lam0 must not alias d_lamT.
+ *          step at a time, keeping every step's first stage, and reversed
+ *          step by step (face-wise reverse mode of the flux, gathered per
+ *          cell; the terms that neighbouring faces share are computed once
+ *          per cell).  d_lam0 must not alias d_lamT.
  * d_ws: sweep_adjoint_workspace_bytes(h, nsteps, ckpt_every) bytes,
  * 256-byte aligned.  Asynchronous on the stream like the other runs.
  */

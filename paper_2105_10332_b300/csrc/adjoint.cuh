@@ -19,7 +19,11 @@
 // its line, and its adjoint input is v_right - v_left; k_face_vjp writes the
 // four cells' contributions of every face and k_gather sums, per cell, the
 // contributions of its eight faces (x faces, then y faces, each in the order
-// of the face's index along its line, wrapped periodically).
+// of the face's index along its line, wrapped periodically).  What several
+// faces share is computed once beforehand, with the same operations in the
+// same order: per cell the pressure, 1/rho and the velocities
+// (k_vjp_cells), per cell and axis the half limiter factors and their
+// derivatives (k_vjp_limiters).
 #pragma once
 
 #include "kernels.cuh"
@@ -92,19 +96,20 @@ __device__ __forceinline__ void limiter_halves_grad(double dm, double dp, int mo
     dhm_dp = fmul(0.5, plus_is_mp ? g_pm_dp : g_mp_dp, F);
 }
 
-// reverse of cell_pressure: add to qb the gradient of pb * P(q)
-__device__ __forceinline__ void cell_pressure_vjp(const double q[4], const EulerConst &k,
-                                                  double pb, double qb[4])
+// reverse of cell_pressure: add to qb the gradient of pb * P(q), given the
+// cell's momenta (mn, mt) in the face-normal frame and its 1/rho and
+// velocities (un, ut) in the same frame
+__device__ __forceinline__ void cell_pressure_vjp(double mn, double mt, double inv, double un,
+                                                  double ut, const EulerConst &k, double pb,
+                                                  double qb[4])
 {
     const Fx &F = k.f;
-    const double inv = __drcp_rn(q[0]);
-    const double u = fmul(q[1], inv, F), v = fmul(q[2], inv, F);
     const double eb = fmul(pb, k.gm1, F);
     const double kb = fmul(fmul(-0.5, k.gm1, F), pb, F);
-    const double ub = fmul(kb, q[1], F), vb = fmul(kb, q[2], F);
-    const double mxb = fadd(fmul(kb, u, F), fmul(ub, inv, F), F);
-    const double myb = fadd(fmul(kb, v, F), fmul(vb, inv, F), F);
-    const double invb = fadd(fmul(ub, q[1], F), fmul(vb, q[2], F), F);
+    const double ub = fmul(kb, mn, F), vb = fmul(kb, mt, F);
+    const double mxb = fadd(fmul(kb, un, F), fmul(ub, inv, F), F);
+    const double myb = fadd(fmul(kb, ut, F), fmul(vb, inv, F), F);
+    const double invb = fadd(fmul(ub, mn, F), fmul(vb, mt, F), F);
     qb[0] = fadd(qb[0], fmul(fmul(-invb, inv, F), inv, F), F);
     qb[1] = fadd(qb[1], mxb, F);
     qb[2] = fadd(qb[2], myb, F);
@@ -112,17 +117,14 @@ __device__ __forceinline__ void cell_pressure_vjp(const double q[4], const Euler
 }
 
 // reverse of state_flux (face-normal frame): add to qb the gradient of
-// <fb, F(q)> + lb * lam(q)
-__device__ __forceinline__ void state_flux_vjp(const double q[4], const EulerConst &k,
-                                               const double fb[4], double lb, double qb[4])
+// <fb, F(q)> + lb * lam(q); s holds the forward pass's intermediates
+__device__ __forceinline__ void state_flux_vjp(const double q[4], const FluxParts &s,
+                                               const EulerConst &k, const double fb[4], double lb,
+                                               double qb[4])
 {
     const Fx &F = k.f;
-    const double inv = __drcp_rn(q[0]);
+    const double inv = s.inv, un = s.un, ut = s.ut, p = s.p, c = s.c;
     const double mn = q[1], mt = q[2], E = q[3];
-    const double un = fmul(mn, inv, F), ut = fmul(mt, inv, F);
-    const double ke2 = __fma_rn(mn, un, fmul(mt, ut, F));
-    const double p = fmul(k.gm1, __fma_rn(-0.5, ke2, E), F);
-    const double c = __dsqrt_rn(fmul(fmul(k.gamma, p, F), inv, F));
     double mnb = fb[0], mtb, Eb, unb, utb, pb, invb;
     // f1 = mn un + p
     mnb = fadd(mnb, fmul(fb[1], un, F), F);
@@ -161,37 +163,37 @@ __device__ __forceinline__ void state_flux_vjp(const double q[4], const EulerCon
 }
 
 // Reverse of the numerical flux at the face between cells 1 and 2 of the
-// line of cells 0..3 (face-normal frame).  a: adjoint of the flux; qb[m]
-// receives the gradient for cell m (zeroed here).
-__device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double a[4],
-                                              const EulerConst &k, int mode, double qb[4][4])
+// line of cells 0..3 (face-normal frame).  q1, q2: the states of cells 1
+// and 2; mn, mt, inv, un, ut: every cell's momenta, 1/rho and velocities in
+// the face-normal frame; lim1 = (h+, dh+/ddm, dh+/ddp) of cell 1 and
+// lim2 = (h-, dh-/ddm, dh-/ddp) of cell 2 along the face's axis.
+// a: adjoint of the flux; qb[m] receives the gradient for cell m (zeroed
+// here).
+__device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q2[4],
+                                              const double mn[4], const double mt[4],
+                                              const double inv[4], const double un[4],
+                                              const double ut[4], const double lim1[3],
+                                              const double lim2[3], const double a[4],
+                                              const EulerConst &k, double qb[4][4])
 {
     const Fx &F = k.f;
-    double p[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        p[m] = cell_pressure(q[m][0], q[m][1], q[m][2], q[m][3], k);
+    for (int m = 0; m < 4; ++m)
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             qb[m][c] = 0.0;
-    }
-    double hl, hl_m, dl_dm, dl_dp, dl2, dl3;
-    double hr_p, hr, dr0, dr1, dr_dm, dr_dp;
-    // cell 1 towards its + face: (dm, dp) = (p1 - p0, p2 - p1)
-    limiter_halves_grad(fadd(p[1], -p[0], F), fadd(p[2], -p[1], F), mode, F, hl, hl_m, dl_dm,
-                        dl_dp, dl2, dl3);
-    // cell 2 towards its - face: (dm, dp) = (p2 - p1, p3 - p2)
-    limiter_halves_grad(fadd(p[2], -p[1], F), fadd(p[3], -p[2], F), mode, F, hr_p, hr, dr0, dr1,
-                        dr_dm, dr_dp);
+    const double hl = lim1[0], dl_dm = lim1[1], dl_dp = lim1[2];
+    const double hr = lim2[0], dr_dm = lim2[1], dr_dp = lim2[2];
     double dq[4], ql[4], qr[4], fl[4], fr[4], laml, lamr;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        dq[c] = fadd(q[2][c], -q[1][c], F);
-        ql[c] = __fma_rn(hl, dq[c], q[1][c]);
-        qr[c] = __fma_rn(-hr, dq[c], q[2][c]);
+        dq[c] = fadd(q2[c], -q1[c], F);
+        ql[c] = __fma_rn(hl, dq[c], q1[c]);
+        qr[c] = __fma_rn(-hr, dq[c], q2[c]);
     }
-    state_flux(ql[0], ql[1], ql[2], ql[3], k, fl, laml);
-    state_flux(qr[0], qr[1], qr[2], qr[3], k, fr, lamr);
+    FluxParts pl, pr;
+    state_flux(ql[0], ql[1], ql[2], ql[3], k, fl, laml, pl);
+    state_flux(qr[0], qr[1], qr[2], qr[3], k, fr, lamr, pr);
     const bool left = __double_as_longlong(laml) > __double_as_longlong(lamr);
     const double r = left ? laml : lamr;
     // Fh_c = 1/2 (r (ql_c - qr_c) + fl_c + fr_c)
@@ -205,8 +207,8 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
         rb = fadd(rb, fmul(fmul(0.5, a[c], F), fadd(ql[c], -qr[c], F), F), F);
     }
     double sl[4] = {0.0, 0.0, 0.0, 0.0}, sr[4] = {0.0, 0.0, 0.0, 0.0};
-    state_flux_vjp(ql, k, flb, left ? rb : 0.0, sl);
-    state_flux_vjp(qr, k, frb, left ? 0.0 : rb, sr);
+    state_flux_vjp(ql, pl, k, flb, left ? rb : 0.0, sl);
+    state_flux_vjp(qr, pr, k, frb, left ? 0.0 : rb, sr);
     double hlb = 0.0, hrb = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -233,16 +235,75 @@ __device__ __forceinline__ void face_flux_vjp(const double q[4][4], const double
     pb[2] = fadd(pb[2], -b2, F);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-        cell_pressure_vjp(q[m], k, pb[m], qb[m]);
+        cell_pressure_vjp(mn[m], mt[m], inv[m], un[m], ut[m], k, pb[m], qb[m]);
+}
+
+// Per cell: cp[0..3][cell] = pressure, 1/rho, u, v (the arithmetic of
+// cell_pressure, whose sum of momentum terms is symmetric in x and y).
+__global__ void __launch_bounds__(kThreads) k_vjp_cells(Params p, const double *q, double *cp)
+{
+    const int64_t plane = p.nx * p.ny;
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= plane)
+        return;
+    const Fx &F = p.ek.f;
+    const double rho = q[cell], mx = q[plane + cell], my = q[2 * plane + cell];
+    const double E = q[3 * plane + cell];
+    const double inv = __drcp_rn(rho);
+    const double u = fmul(mx, inv, F), v = fmul(my, inv, F);
+    const double ke2 = fadd(fmul(mx, u, F), fmul(my, v, F), F);
+    cp[cell] = fmul(p.ek.gm1, __fma_rn(-0.5, ke2, E), F);
+    cp[plane + cell] = inv;
+    cp[2 * plane + cell] = u;
+    cp[3 * plane + cell] = v;
+}
+
+// Per cell and axis: lp[(axis*6 + t)*plane + cell] = h+, dh+/ddm, dh+/ddp,
+// h-, dh-/ddm, dh-/ddp of the cell's half limiter factors, from
+// dm = P_i - P_{i-1} and dp = P_{i+1} - P_i along the axis.
+__global__ void __launch_bounds__(kThreads) k_vjp_limiters(Params p, const double *cp, double *lp)
+{
+    const int64_t plane = p.nx * p.ny;
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= plane)
+        return;
+    const Fx &F = p.ek.f;
+    const int64_t i = cell % p.nx, j = cell / p.nx;
+    const int64_t im = i == 0 ? p.nx - 1 : i - 1, ip = i == p.nx - 1 ? 0 : i + 1;
+    const int64_t jm = j == 0 ? p.ny - 1 : j - 1, jp = j == p.ny - 1 ? 0 : j + 1;
+    const double pc = cp[cell];
+    const double nb[2][2] = {{cp[j * p.nx + im], cp[j * p.nx + ip]},
+                             {cp[jm * p.nx + i], cp[jp * p.nx + i]}};
+#pragma unroll
+    for (int axis = 0; axis < 2; ++axis) {
+        double hp, hm, dp_dm, dp_dp, dm_dm, dm_dp;
+        limiter_halves_grad(fadd(pc, -nb[axis][0], F), fadd(nb[axis][1], -pc, F), p.literal, F,
+                            hp, hm, dp_dm, dp_dp, dm_dm, dm_dp);
+        double *o = lp + (int64_t)axis * 6 * plane + cell;
+        o[0] = hp;
+        o[plane] = dp_dm;
+        o[2 * plane] = dp_dp;
+        o[3 * plane] = hm;
+        o[4 * plane] = dm_dm;
+        o[5 * plane] = dm_dp;
+    }
 }
 
 // Per face (axis 0: between (i,j) and (i+1,j); axis 1: between (i,j) and
 // (i,j+1)): the contributions of <v_right - v_left, Fh(Q)> to the gradient of
 // the four cells of its line.  fo[(axis*16 + m*4 + c) * plane + j*nx + i],
 // cell m = 0..3 at offset m-1 along the axis, component c in the
-// (rho, m_x, m_y, E) order.
-__global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q, const double *v,
-                                                       double *fo)
+// (rho, m_x, m_y, E) order.  cp, lp: k_vjp_cells and k_vjp_limiters of q.
+// 128-thread CTAs held to 128 registers: four CTAs (16 warps) per SM, where
+// the 138 registers the compiler would otherwise take leave room for one
+// 256-thread CTA (8 warps) to hide the long divide and square-root chains.
+#ifndef SWEEP_VJP_THREADS
+#define SWEEP_VJP_THREADS 128
+#endif
+constexpr int kVjpThreads = SWEEP_VJP_THREADS;
+__global__ void __launch_bounds__(kVjpThreads, 512 / kVjpThreads)
+    k_face_vjp(Params p, const double *q, const double *cp, const double *lp, const double *v,
+               double *fo)
 {
     const int64_t plane = p.nx * p.ny;
     const Fx F = p.ek.f;
@@ -254,8 +315,8 @@ __global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q
     const int64_t i = cell % p.nx, j = cell / p.nx;
     // normal-frame component order: (rho, m_n, m_t, E)
     const int c1 = axis == 0 ? 1 : 2, c2 = axis == 0 ? 2 : 1;
-    double qq[4][4];
     int64_t idx[4];
+    double mn[4], mt[4], inv[4], un[4], ut[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         int64_t ii = i, jj = j;
@@ -267,17 +328,23 @@ __global__ void __launch_bounds__(kThreads) k_face_vjp(Params p, const double *q
             jj = jj < 0 ? jj + p.ny : (jj >= p.ny ? jj - p.ny : jj);
         }
         idx[m] = jj * p.nx + ii;
-        qq[m][0] = q[idx[m]];
-        qq[m][1] = q[c1 * plane + idx[m]];
-        qq[m][2] = q[c2 * plane + idx[m]];
-        qq[m][3] = q[3 * plane + idx[m]];
+        mn[m] = q[c1 * plane + idx[m]];
+        mt[m] = q[c2 * plane + idx[m]];
+        inv[m] = cp[plane + idx[m]];
+        un[m] = cp[(1 + c1) * plane + idx[m]];
+        ut[m] = cp[(1 + c2) * plane + idx[m]];
     }
+    const double q1[4] = {q[idx[1]], mn[1], mt[1], q[3 * plane + idx[1]]};
+    const double q2[4] = {q[idx[2]], mn[2], mt[2], q[3 * plane + idx[2]]};
+    const double *L = lp + (int64_t)axis * 6 * plane;
+    const double lim1[3] = {L[idx[1]], L[plane + idx[1]], L[2 * plane + idx[1]]};
+    const double lim2[3] = {L[3 * plane + idx[2]], L[4 * plane + idx[2]], L[5 * plane + idx[2]]};
     const double a[4] = {fadd(v[idx[2]], -v[idx[1]], F),
                          fadd(v[c1 * plane + idx[2]], -v[c1 * plane + idx[1]], F),
                          fadd(v[c2 * plane + idx[2]], -v[c2 * plane + idx[1]], F),
                          fadd(v[3 * plane + idx[2]], -v[3 * plane + idx[1]], F)};
     double qb[4][4];
-    face_flux_vjp(qq, a, p.ek, p.literal, qb);
+    face_flux_vjp(q1, q2, mn, mt, inv, un, ut, lim1, lim2, a, p.ek, qb);
     double *o = fo + (int64_t)axis * 16 * plane + cell;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {

@@ -706,9 +706,11 @@ __global__ void __launch_bounds__(kThreads) k_octahedron(Params p, int64_t base,
 
 // One RK2 step of the Standard solver: block (I, J) of edge T = std_tile
 // loads its tile plus a 2n halo, takes stage 1 on the tile plus an n halo
-// and stage 2 on the tile, and writes the tile to dst.
+// and stage 2 on the tile, and writes the tile to dst (and, if qstar is
+// not null, the tile's first-stage values to qstar).
 template <class EQ>
-__global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *src, double *dst)
+__global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *src, double *dst,
+                                                       double *qstar)
 {
     extern __shared__ double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 4 * n;
@@ -728,6 +730,13 @@ __global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *s
     __syncthreads();
     Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
+    if (qstar)
+        for_rect({2 * n, wp - 2 * n, 2 * n, wp - 2 * n}, [&](int x, int y) {
+            const int64_t g = gidx(p, B.ox, B.oy, x, y);
+#pragma unroll
+            for (int c = 0; c < EQ::NC; ++c)
+                qstar[c * gplane + g] = B.buf[1][c * B.plane + y * wp + x];
+        });
     Stage<EQ, 1>::run(p, B, 2, {2 * n, wp - 2 * n, 2 * n, wp - 2 * n});
     __syncthreads();
     for_rect({2 * n, wp - 2 * n, 2 * n, wp - 2 * n}, [&](int x, int y) {

@@ -110,21 +110,34 @@ __device__ __forceinline__ void limiter_halves(double dm, double dp, int literal
 // inv = 1/rho, u_n = m_n inv, u_t = m_t inv,
 // p = (gamma-1) fma(-1/2, fma(m_n, u_n, m_t u_t), E), c = sqrt((gamma p) inv),
 // f = (m_n, fma(m_n, u_n, p), m_t u_n, (E + p) u_n), lam = |u_n| + c.
+// The intermediate values of one state flux (a reverse pass reuses them).
+struct FluxParts {
+    double inv, un, ut, p, c;
+};
+
+__device__ __forceinline__ void state_flux(double rho, double mn, double mt, double E,
+                                           const EulerConst &k, double f[4], double &lam,
+                                           FluxParts &s)
+{
+    const Fx &x = k.f;
+    s.inv = __drcp_rn(rho);  // correctly rounded, equal to 1.0 / rho
+    s.un = fmul(mn, s.inv, x);
+    s.ut = fmul(mt, s.inv, x);
+    const double ke2 = __fma_rn(mn, s.un, fmul(mt, s.ut, x));
+    s.p = fmul(k.gm1, __fma_rn(-0.5, ke2, E), x);
+    s.c = __dsqrt_rn(fmul(fmul(k.gamma, s.p, x), s.inv, x));
+    f[0] = mn;
+    f[1] = __fma_rn(mn, s.un, s.p);
+    f[2] = fmul(mt, s.un, x);
+    f[3] = fmul(fadd(E, s.p, x), s.un, x);
+    lam = fadd(fabs(s.un), s.c, x);
+}
+
 __device__ __forceinline__ void state_flux(double rho, double mn, double mt, double E,
                                            const EulerConst &k, double f[4], double &lam)
 {
-    const Fx &x = k.f;
-    const double inv = __drcp_rn(rho);  // correctly rounded, equal to 1.0 / rho
-    const double un = fmul(mn, inv, x);
-    const double ut = fmul(mt, inv, x);
-    const double ke2 = __fma_rn(mn, un, fmul(mt, ut, x));
-    const double p = fmul(k.gm1, __fma_rn(-0.5, ke2, E), x);
-    const double c = __dsqrt_rn(fmul(fmul(k.gamma, p, x), inv, x));
-    f[0] = mn;
-    f[1] = __fma_rn(mn, un, p);
-    f[2] = fmul(mt, un, x);
-    f[3] = fmul(fadd(E, p, x), un, x);
-    lam = fadd(fabs(un), c, x);
+    FluxParts s;
+    state_flux(rho, mn, mt, E, k, f, lam, s);
 }
 
 // larger of two non-negative, non-NaN doubles by their bit patterns (integer

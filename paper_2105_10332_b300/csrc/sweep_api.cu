@@ -160,7 +160,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
-            k_standard<EQ><<<grid, kThreads, smem, st>>>(p, a, b);
+            k_standard<EQ><<<grid, kThreads, smem, st>>>(p, a, b, nullptr);
         }
         double *t = a;
         a = b;
@@ -288,7 +288,7 @@ int run_standard_any(const sweep_s *h, Params p, int64_t nsteps, cudaStream_t st
 // ------------------------------------------------------------ adjoint
 
 struct AdjLayout {
-    size_t store, ckpt, seg, qs, mu, faces, total;  // byte offsets (after the header)
+    size_t store, ckpt, seg, qs, mu, cp, lp, faces, total;  // byte offsets (after the header)
     int64_t nseg, ckpt_every;
 };
 
@@ -308,12 +308,17 @@ AdjLayout adjoint_layout(const sweep_s *h, int64_t nsteps, int64_t ckpt)
     off += st * (size_t)(L.nseg > 0 ? L.nseg : 1);
     L.seg = off;
     off += st * (size_t)ckpt;
-    L.qs = off;
-    off += st;
+    L.qs = off;  // first-stage states of the segment
+    off += st * (size_t)ckpt;
     L.mu = off;
     off += st;
+    const size_t plane = sizeof(double) * (size_t)h->nx * (size_t)h->ny;
+    L.cp = off;
+    off += (plane * 4 + 255) / 256 * 256;
+    L.lp = off;
+    off += (plane * 12 + 255) / 256 * 256;
     L.faces = off;
-    off += sizeof(double) * 32 * (size_t)h->nx * (size_t)h->ny;
+    off += plane * 32;
     L.total = off;
     return L;
 }
@@ -327,7 +332,9 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
     const size_t sstride = sizeof(double) * (size_t)slot_elems(h);
     auto ckpt_ptr = [&](int64_t s) { return (double *)(base + L.ckpt + sstride * (size_t)s); };
     auto seg_ptr = [&](int64_t t) { return (double *)(base + L.seg + sstride * (size_t)t); };
-    double *qs = (double *)(base + L.qs), *mu = (double *)(base + L.mu);
+    auto qs_ptr = [&](int64_t t) { return (double *)(base + L.qs + sstride * (size_t)t); };
+    double *mu = (double *)(base + L.mu);
+    double *cp = (double *)(base + L.cp), *lp = (double *)(base + L.lp);
     double *faces = (double *)(base + L.faces);
     if (cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return SWEEP_ECUDA;
@@ -346,26 +353,29 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
     Params p = make_params(h, nullptr, ws);
     const int T = h->std_tile;
     const size_t smem_std = smem_bytes<Euler>(T + 4 * Euler::N, 1);
-    const size_t smem_s1 = smem_bytes<Euler>(T + 2 * Euler::N, 1);
-    if (set_smem(k_standard<Euler>, smem_std) != cudaSuccess ||
-        set_smem(k_level1<Euler>, smem_s1) != cudaSuccess)
-        return SWEEP_ECUDA;
+    if (set_smem(k_standard<Euler>, smem_std) != cudaSuccess) return SWEEP_ECUDA;
     const unsigned tiles = (unsigned)((h->nx / T) * (h->ny / T));
     const int64_t plane = h->nx * h->ny;
-    const unsigned gf = (unsigned)((2 * plane + kThreads - 1) / kThreads);
+    const unsigned gf = (unsigned)((2 * plane + kVjpThreads - 1) / kVjpThreads);
     const unsigned gc = (unsigned)((plane + kThreads - 1) / kThreads);
     for (int64_t s = L.nseg - 1; s >= 0; --s) {
         const int64_t len = (s + 1) * ckpt <= nsteps ? ckpt : nsteps - s * ckpt;
         if (cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess)
             return SWEEP_ECUDA;
-        for (int64_t t = 0; t + 1 < len; ++t)
-            k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(p, seg_ptr(t), seg_ptr(t + 1));
+        // recompute the segment, keeping each step's first stage Q*; the
+        // last step's end state is not needed and lands in mu (unused yet)
+        for (int64_t t = 0; t < len; ++t)
+            k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(
+                p, seg_ptr(t), t + 1 < len ? seg_ptr(t + 1) : mu, qs_ptr(t));
         for (int64_t t = len - 1; t >= 0; --t) {
-            k_level1<Euler><<<tiles, kThreads, smem_s1, st>>>(p, seg_ptr(t), qs);
-            k_face_vjp<<<gf, kThreads, 0, st>>>(p, qs, lam0, faces);
+            k_vjp_cells<<<gc, kThreads, 0, st>>>(p, qs_ptr(t), cp);
+            k_vjp_limiters<<<gc, kThreads, 0, st>>>(p, cp, lp);
+            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, qs_ptr(t), cp, lp, lam0, faces);
             k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 0);
-            k_face_vjp<<<gf, kThreads, 0, st>>>(p, seg_ptr(t), mu, faces);
+            k_vjp_cells<<<gc, kThreads, 0, st>>>(p, seg_ptr(t), cp);
+            k_vjp_limiters<<<gc, kThreads, 0, st>>>(p, cp, lp);
+            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, seg_ptr(t), cp, lp, mu, faces);
             k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 1);
         }
         if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
