@@ -154,6 +154,44 @@ def dist_setup():
     return world, rank, local
 
 
+class Replicas:
+    """N independent replicas, one per rank (torchrun).  The solver exchanges
+    nothing between ranks, so the only collectives are the barriers around the
+    timed region and the max of the per-rank times.  backend: "nccl" on GPUs
+    ("gloo" on CPU); device: where the reduced value lives."""
+
+    def __init__(self, backend, device):
+        self.world, self.rank, self.local = dist_setup()
+        self.device = device
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {"device_id": device} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+            self._torch, self._dist = torch, dist
+
+    def barrier(self):
+        if self.world > 1:
+            self._dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return x
+        t = self._torch.tensor([float(x)], dtype=self._torch.float64, device=self.device)
+        self._dist.all_reduce(t, op=self._dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self._dist.destroy_process_group()
+
+
+def job_rate(world, cells, nsteps, runs, seconds):
+    """Whole-job Gcell-steps/s: each of `world` replicas advanced `cells` cells
+    by `nsteps` steps `runs` times within `seconds` (the slowest rank's time)."""
+    return world * cells * nsteps * runs / seconds / 1e9
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -217,6 +255,8 @@ def run_batch(args, wl):
     from the autotuner per (equation, size class).  One bench step = one
     replay of the captured batch graph; the baseline runs each instance alone,
     one after another."""
+    if dist_setup()[1] != 0:
+        return  # a single-GPU measurement: under torchrun rank 0 alone runs it
     import torch
     from paper_2105_10332_b300 import autotune, sweep as S, workloads as W
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -294,6 +334,8 @@ def run_adjoint(args, wl):
     step = one sweep_adjoint call (checkpointed swept forward pass + reverse
     pass).  Reports Gcell-steps/s of the gradient and its time over the plain
     swept forward run."""
+    if dist_setup()[1] != 0:
+        return  # a single-GPU measurement: under torchrun rank 0 alone runs it
     import torch
     from paper_2105_10332_b300 import sweep as S
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -340,16 +382,10 @@ def run_ours(args, wl):
     import torch
     from paper_2105_10332_b300 import sweep as S
     world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    rep = Replicas("nccl", dev)
+    barrier = rep.barrier
 
     solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"])
     N, cells = wl["nsteps"], wl["nx"] * wl["ny"]
@@ -389,12 +425,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize(dev)
         return sum(a.elapsed_time(b) for a, b in evs)
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rep.max
 
     # warm-up (untimed), including the graph captures
     for _ in range(args.warmup):
@@ -447,9 +478,9 @@ def run_ours(args, wl):
     e2e_s = max_over_ranks(e2e_s)
     state_bytes = init.numel() * 8
 
-    value = world * cells * N * args.steps / (ms_swept / 1e3) / 1e9
-    v_std = world * cells * N * args.steps / (ms_std / 1e3) / 1e9
-    v_e2e = world * cells * N * K_e2e / e2e_s / 1e9
+    value = job_rate(world, cells, N, args.steps, ms_swept / 1e3)
+    v_std = job_rate(world, cells, N, args.steps, ms_std / 1e3)
+    v_e2e = job_rate(world, cells, N, K_e2e, e2e_s)
 
     # roofline of the dominant kernel (FP64 ALU bound)
     tiles = (wl["nx"] // wl["tile"]) * (wl["ny"] // wl["tile"])
@@ -494,8 +525,7 @@ def run_ours(args, wl):
                 "gpu_launches": int(launches_per_run * args.steps),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "clocks": clocks}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    rep.close()
 
 
 def main():
