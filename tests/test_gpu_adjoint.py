@@ -126,3 +126,40 @@ def test_autograd_function(torch_cuda, oracle_lib):
     lamT[0] = 2.0 * (ref_qN[0] - target.cpu().numpy())
     ref = oracle_lib.euler_adjoint(q0, lamT, dt, dx, 12, ckpt=5)
     assert relerr(q.grad.cpu().numpy(), ref) <= 1e-12
+
+
+def test_euler_adjoint_config4_full_size(torch_cuda):
+    """Config 4 at its full size, as bench.py runs it (1024^2 vortex, 2000
+    steps, checkpoints every 64, unlimited reconstruction, loss
+    sum((rho_T - rho_target)^2)): the gradient against central differences of
+    the GPU forward solver along 3 seeded directions, h = 1e-6 (measured
+    relative gaps 2e-8 .. 3e-9)."""
+    torch = torch_cuda
+    import bench
+    from paper_2105_10332_b300 import sweep as S
+    wl = bench.workload("adjoint1024")
+    s = S.Solver("euler", wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"],
+                 limiter=wl["limiter"])
+    N, K = wl["nsteps"], wl["ckpt"]
+    q0 = torch.from_numpy(wl["state"]).cuda()
+    target = torch.from_numpy(wl["target"]).cuda()
+
+    def loss(q):
+        qq = q.clone()
+        s.run_swept(qq, N)
+        return float(torch.sum((qq[0] - target) ** 2))
+
+    qN = q0.clone()
+    s.run_swept(qN, N)
+    lamT = torch.zeros_like(q0)
+    lamT[0] = 2.0 * (qN[0] - target)
+    g = s.adjoint(q0, lamT, N, K)
+    gen = torch.Generator(device="cuda").manual_seed(20210521)
+    h = 1e-6
+    errs = []
+    for _ in range(3):
+        d = torch.randn(q0.shape, generator=gen, device="cuda", dtype=torch.float64)
+        fd = (loss(q0 + h * d) - loss(q0 - h * d)) / (2 * h)
+        ad = float(torch.sum(g * d))
+        errs.append(abs(fd - ad) / abs(ad))
+    assert max(errs) <= 1e-6, errs

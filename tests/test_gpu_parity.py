@@ -252,3 +252,35 @@ def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, passes, eq
                 ref = oracle_lib.heat_run(q0, s.get("r"), N)
             got = gpu_run(torch_cuda, s, q0, N, "run_swept")
             assert np.array_equal(got, ref), (cluster, d, N, relerr(got, ref))
+
+
+def test_heat_config3_full_size(torch_cuda):
+    """Config 3 at its full size and in the launch configuration bench.py
+    times (16384^2, 2000 steps, block 64, depth 30): Swept = Standard
+    bitwise, and 256 sampled cells match the discrete closed form
+    (measured gap 5.5e-14 of max|u0|)."""
+    from paper_2105_10332_b300 import sweep as S
+    torch = torch_cuda
+    n, N = 16384, 2000
+    dt, dx = W.heat_dt(n, 0.1)
+    s = S.Solver("heat", n, n, dt, dx, 64, 30)
+    r = s.get("r")
+    u0 = W.heat_modes(n, n)
+    a = torch.from_numpy(u0).cuda()
+    b = a.clone()
+    s.run_swept(a, N)
+    s.run_standard(b, N)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    del b
+    rng = np.random.default_rng(3)
+    js, is_ = rng.integers(0, n, 256), rng.integers(0, n, 256)
+    got = a[torch.from_numpy(js).cuda(), torch.from_numpy(is_).cuda()].cpu().numpy()
+    x, y = W.heat_grid(n, n)
+    exp = np.zeros(256)
+    for amp, kx, ky, phx, phy in W.heat_modes_spec():
+        lam = -4 * (math.sin(math.pi * kx / n) ** 2 + math.sin(math.pi * ky / n) ** 2)
+        z = r * lam
+        G = 1 + z + 0.5 * z * z
+        exp += amp * G ** N * np.sin(2 * math.pi * ky * y[js] + phy) * np.sin(2 * math.pi * kx * x[is_] + phx)
+    assert np.max(np.abs(got - exp)) <= 1e-12 * np.max(np.abs(u0))
