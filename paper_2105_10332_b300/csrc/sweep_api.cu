@@ -50,6 +50,7 @@ int64_t slot_elems(const sweep_s *h)
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int64_t kStdMinBlocks = 148;  // SMs of a B300
 
 // shared-memory bytes of a swept CTA / a Standard CTA
 size_t swept_smem(int eqn, int b, int C)
@@ -432,12 +433,23 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->passes = 1;
     h->profile = 0;
     h->ev_used = 0;
+    // Standard block edge: the first preferred edge that gives at least one
+    // block per SM (148 on B300), else the allowed edge with the most blocks
+    // (a small grid is latency bound: more, smaller blocks finish sooner)
     const int prefer[] = {eqn == SWEEP_HEAT ? 32 : 16, 16, 8, 24, 12, 64, 48, 40, 20, 10};
-    for (int t : prefer)
-        if (valid_std_tile(h, t)) {
+    int64_t most = 0;
+    for (int t : prefer) {
+        if (!valid_std_tile(h, t)) continue;
+        const int64_t blocks = (nx / t) * (ny / t);
+        if (blocks >= kStdMinBlocks) {
             h->std_tile = t;
             break;
         }
+        if (blocks > most) {
+            most = blocks;
+            h->std_tile = t;
+        }
+    }
     if (h->std_tile == 0) {
         delete h;
         return SWEEP_EINVAL;
