@@ -810,9 +810,14 @@ static void limiter_grad(int limiter, int plus, double dm, double dp, double *d_
 
 /* Reverse of face_flux at the face between cells 0 and 1 of the line
  * (-1, 0, 1, 2), states in the face-normal frame.  a[4]: adjoint of the
- * numerical flux.  Accumulates into qbar[m][4] for m = 0..3 (cells -1..2). */
+ * numerical flux.  Accumulates into qbar[1] and qbar[2] (cells 0 and 1) the
+ * gradient through the reconstructed states, and returns in pbar[m] the
+ * adjoint of the cell pressure P(q[m]) of each of the four cells (the
+ * limiter's inputs).  The pressure's own reverse (cell_pressure_bar) is
+ * linear in pbar and the same for every face of a cell, so the callers
+ * apply it once per cell to the summed pbar. */
 static void face_flux_bar(const double *q[4], double gamma, int limiter, const double a[4],
-                          double qbar[4][4])
+                          double qbar[4][4], double pbar[4])
 {
     double p[4];
     for (int m = 0; m < 4; ++m)
@@ -858,7 +863,9 @@ static void face_flux_bar(const double *q[4], double gamma, int limiter, const d
         qbar[2][k] += qrbar[k] + dqbar;
     }
     /* hl = phi0p / 2 from (p0 - pm1, p1 - p0); hr = phi1m / 2 from (p1 - p0, p2 - p1) */
-    double pbar[4] = {0, 0, 0, 0}, g_dm, g_dp;
+    double g_dm, g_dp;
+    for (int m = 0; m < 4; ++m)
+        pbar[m] = 0.0;
     limiter_grad(limiter, 1, p[1] - p[0], p[2] - p[1], &g_dm, &g_dp);
     pbar[1] += 0.5 * hlbar * g_dm;
     pbar[0] -= 0.5 * hlbar * g_dm;
@@ -869,18 +876,21 @@ static void face_flux_bar(const double *q[4], double gamma, int limiter, const d
     pbar[1] -= 0.5 * hrbar * g_dm;
     pbar[3] += 0.5 * hrbar * g_dp;
     pbar[2] -= 0.5 * hrbar * g_dp;
-    for (int m = 0; m < 4; ++m)
-        cell_pressure_bar(q[m], gamma, pbar[m], qbar[m]);
 }
 
 /* out = J^T v for the residual d(Q)_c = (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2}
- * - Gh_{j+1/2}) of every cell (out is overwritten).  Each face adds its
- * contribution a = v_{right} - v_{left} through face_flux_bar. */
-static void euler_residual_vjp(const double *q, const double *v, double *out, int64_t nx,
-                               int64_t ny, double gamma, int limiter)
+ * - Gh_{j+1/2}) of every cell (out is overwritten).  Each face, visited x
+ * faces then y faces in raster order, adds its contribution for
+ * a = v_{right} - v_{left} through face_flux_bar: the gradient through its
+ * reconstructed states to its two cells' out, and the adjoints of its four
+ * cells' pressures to pb (plane doubles, scratch).  Then every cell adds
+ * the reverse of its pressure for the summed pb. */
+static void euler_residual_vjp(const double *q, const double *v, double *out, double *pb,
+                               int64_t nx, int64_t ny, double gamma, int limiter)
 {
     const int64_t plane = nx * ny;
     memset(out, 0, sizeof(double) * (size_t)(4 * plane));
+    memset(pb, 0, sizeof(double) * (size_t)plane);
     for (int axis = 0; axis < 2; ++axis)
         for (int64_t j = 0; j < ny; ++j)
             for (int64_t i = 0; i < nx; ++i) {
@@ -902,14 +912,23 @@ static void euler_residual_vjp(const double *q, const double *v, double *out, in
                     const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
                     a[k] = v[kk * plane + cr] - v[kk * plane + cl];
                 }
-                double qb[4][4] = {{0}};
-                face_flux_bar(qp, gamma, limiter, a, qb);
-                for (int m = 0; m < 4; ++m)
+                double qb[4][4] = {{0}}, pbar[4];
+                face_flux_bar(qp, gamma, limiter, a, qb, pbar);
+                for (int m = 1; m <= 2; ++m)
                     for (int k = 0; k < 4; ++k) {
                         const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
                         out[kk * plane + idx[m]] += qb[m][k];
                     }
+                for (int m = 0; m < 4; ++m)
+                    pb[idx[m]] += pbar[m];
             }
+    for (int64_t c = 0; c < plane; ++c) {
+        const double qc[4] = {q[c], q[plane + c], q[2 * plane + c], q[3 * plane + c]};
+        double ob[4] = {out[c], out[plane + c], out[2 * plane + c], out[3 * plane + c]};
+        cell_pressure_bar(qc, gamma, pb[c], ob);
+        for (int k = 0; k < 4; ++k)
+            out[k * plane + c] = ob[k];
+    }
 }
 
 /* One adjoint RK2 step at Q^n (RK2: Q* = Q + lam1 d(Q), Q' = Q + lam2 d(Q*)):
@@ -917,14 +936,14 @@ static void euler_residual_vjp(const double *q, const double *v, double *out, in
  *   lam  = lam' + mu* + lam1 J(Q)^T mu*                                  */
 static void euler_adjoint_step(const double *q, double *lam, int64_t nx, int64_t ny, double lam1,
                                double lam2, double gamma, int limiter, double *qs, double *ms,
-                               double *tmp)
+                               double *tmp, double *pb)
 {
     const int64_t n4 = 4 * nx * ny;
     euler_stage(nx, ny, lam1, gamma, limiter, q, q, qs); /* Q* */
-    euler_residual_vjp(qs, lam, tmp, nx, ny, gamma, limiter);
+    euler_residual_vjp(qs, lam, tmp, pb, nx, ny, gamma, limiter);
     for (int64_t k = 0; k < n4; ++k)
         ms[k] = lam2 * tmp[k];
-    euler_residual_vjp(q, ms, tmp, nx, ny, gamma, limiter);
+    euler_residual_vjp(q, ms, tmp, pb, nx, ny, gamma, limiter);
     for (int64_t k = 0; k < n4; ++k)
         lam[k] = lam[k] + ms[k] + lam1 * tmp[k];
 }
@@ -944,12 +963,14 @@ int oracle_euler_adjoint(int64_t nx, int64_t ny, double dt, double dx, double ga
     double *qs = (double *)malloc(sizeof(double) * n4);
     double *ms = (double *)malloc(sizeof(double) * n4);
     double *tmp = (double *)malloc(sizeof(double) * n4);
-    if (!cps || !seg || !qs || !ms || !tmp) {
+    double *pb = (double *)malloc(sizeof(double) * (size_t)(nx * ny));
+    if (!cps || !seg || !qs || !ms || !tmp || !pb) {
         free(cps);
         free(seg);
         free(qs);
         free(ms);
         free(tmp);
+        free(pb);
         return ORACLE_ENOMEM;
     }
     const double lam2 = dt / dx, lam1 = 0.5 * lam2;
@@ -975,13 +996,14 @@ int oracle_euler_adjoint(int64_t nx, int64_t ny, double dt, double dx, double ga
         }
         for (int64_t t = len - 1; t >= 0; --t)
             euler_adjoint_step(seg + (size_t)t * n4, lam, nx, ny, lam1, lam2, gamma, limiter, qs,
-                               ms, tmp);
+                               ms, tmp, pb);
     }
     free(cps);
     free(seg);
     free(qs);
     free(ms);
     free(tmp);
+    free(pb);
     return ORACLE_OK;
 }
 
@@ -991,8 +1013,10 @@ void oracle_face_flux_vjp(const double *qm1, const double *q0, const double *q1,
                           double gamma, int limiter, const double *a, double *qbar)
 {
     const double *q[4] = {qm1, q0, q1, q2};
-    double qb[4][4] = {{0}};
-    face_flux_bar(q, gamma, limiter, a, qb);
+    double qb[4][4] = {{0}}, pbar[4];
+    face_flux_bar(q, gamma, limiter, a, qb, pbar);
+    for (int m = 0; m < 4; ++m)
+        cell_pressure_bar(q[m], gamma, pbar[m], qb[m]);
     for (int m = 0; m < 4; ++m)
         for (int k = 0; k < 4; ++k)
             qbar[4 * m + k] += qb[m][k];

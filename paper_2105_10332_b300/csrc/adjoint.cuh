@@ -18,12 +18,16 @@
 // is assembled face by face: each face's flux depends on the four cells of
 // its line, and its adjoint input is v_right - v_left; k_face_vjp writes the
 // four cells' contributions of every face and k_gather sums, per cell, the
-// contributions of its eight faces (x faces, then y faces, each in the order
-// of the face's index along its line, wrapped periodically).  What several
-// faces share is computed once beforehand, with the same operations in the
-// same order: per cell the pressure, 1/rho and the velocities
-// (k_vjp_cells), per cell and axis the half limiter factors and their
-// derivatives (k_vjp_limiters).
+// contributions of its faces (x faces, then y faces, each in the order of
+// the face's index along its line, wrapped periodically).  A face's flux
+// reaches its two cells through the reconstructed states and all four cells
+// of its line through the limiter's pressures; the pressure's own reverse is
+// linear in the pressure adjoint and the same for every face of a cell, so
+// the faces hand over pressure adjoints and k_gather applies that reverse
+// once per cell to their sum.  What several faces share is computed once
+// beforehand, with the same operations in the same order: per cell the
+// pressure, 1/rho and the velocities (k_vjp_cells), per cell and axis the
+// half limiter factors and their derivatives (k_vjp_limiters).
 #pragma once
 
 #include "kernels.cuh"
@@ -117,13 +121,15 @@ __device__ __forceinline__ void cell_pressure_vjp(double mn, double mt, double i
 }
 
 // reverse of state_flux (face-normal frame): add to qb the gradient of
-// <fb, F(q)> + lb * lam(q); s holds the forward pass's intermediates
+// <fb, F(q)> + lb * lam(q); s holds the forward pass's intermediates and sb
+// the adjoint of c^2 = (gamma p) inv, lb / (2c) (0 where lb or c is 0),
+// which the caller forms once for the one state that carries lb
 __device__ __forceinline__ void state_flux_vjp(const double q[4], const FluxParts &s,
                                                const EulerConst &k, const double fb[4], double lb,
-                                               double qb[4])
+                                               double sb, double qb[4])
 {
     const Fx &F = k.f;
-    const double inv = s.inv, un = s.un, ut = s.ut, p = s.p, c = s.c;
+    const double inv = s.inv, un = s.un, ut = s.ut, p = s.p;
     const double mn = q[1], mt = q[2], E = q[3];
     double mnb = fb[0], mtb, Eb, unb, utb, pb, invb;
     // f1 = mn un + p
@@ -140,7 +146,6 @@ __device__ __forceinline__ void state_flux_vjp(const double q[4], const FluxPart
     // lam = |un| + c
     unb = fadd(unb, un > 0.0 ? lb : (un < 0.0 ? -lb : 0.0), F);
     // c = sqrt(s), s = (gamma p) inv
-    const double sb = c > 0.0 ? __ddiv_rn(lb, fmul(2.0, c, F)) : 0.0;
     pb = fadd(pb, fmul(fmul(sb, k.gamma, F), inv, F), F);
     invb = fmul(fmul(sb, k.gamma, F), p, F);
     // p = g1 (E - ke2/2)
@@ -164,24 +169,16 @@ __device__ __forceinline__ void state_flux_vjp(const double q[4], const FluxPart
 
 // Reverse of the numerical flux at the face between cells 1 and 2 of the
 // line of cells 0..3 (face-normal frame).  q1, q2: the states of cells 1
-// and 2; mn, mt, inv, un, ut: every cell's momenta, 1/rho and velocities in
-// the face-normal frame; lim1 = (h+, dh+/ddm, dh+/ddp) of cell 1 and
-// lim2 = (h-, dh-/ddm, dh-/ddp) of cell 2 along the face's axis.
-// a: adjoint of the flux; qb[m] receives the gradient for cell m (zeroed
-// here).
+// and 2; lim1 = (h+, dh+/ddm, dh+/ddp) of cell 1 and lim2 = (h-, dh-/ddm,
+// dh-/ddp) of cell 2 along the face's axis; a: adjoint of the flux.
+// qb[0], qb[1] receive the gradient for cells 1 and 2 through the
+// reconstructed states, pb[m] the adjoint of cell m's pressure.
 __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q2[4],
-                                              const double mn[4], const double mt[4],
-                                              const double inv[4], const double un[4],
-                                              const double ut[4], const double lim1[3],
-                                              const double lim2[3], const double a[4],
-                                              const EulerConst &k, double qb[4][4])
+                                              const double lim1[3], const double lim2[3],
+                                              const double a[4], const EulerConst &k,
+                                              double qb[2][4], double pb[4])
 {
     const Fx &F = k.f;
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            qb[m][c] = 0.0;
     const double hl = lim1[0], dl_dm = lim1[1], dl_dp = lim1[2];
     const double hr = lim2[0], dr_dm = lim2[1], dr_dp = lim2[2];
     double dq[4], ql[4], qr[4], fl[4], fr[4], laml, lamr;
@@ -206,9 +203,12 @@ __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q
         qrb[c] = fmul(fmul(-0.5, r, F), a[c], F);
         rb = fadd(rb, fmul(fmul(0.5, a[c], F), fadd(ql[c], -qr[c], F), F), F);
     }
+    // r = lam of one state: only that state's sound speed carries rb
+    const double cm = left ? pl.c : pr.c;
+    const double sbm = cm > 0.0 ? __ddiv_rn(rb, fmul(2.0, cm, F)) : 0.0;
     double sl[4] = {0.0, 0.0, 0.0, 0.0}, sr[4] = {0.0, 0.0, 0.0, 0.0};
-    state_flux_vjp(ql, pl, k, flb, left ? rb : 0.0, sl);
-    state_flux_vjp(qr, pr, k, frb, left ? 0.0 : rb, sr);
+    state_flux_vjp(ql, pl, k, flb, left ? rb : 0.0, left ? sbm : 0.0, sl);
+    state_flux_vjp(qr, pr, k, frb, left ? 0.0 : rb, left ? 0.0 : sbm, sr);
     double hlb = 0.0, hrb = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -218,11 +218,13 @@ __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q
         const double dqb = fadd(fmul(qlb[c], hl, F), -fmul(qrb[c], hr, F), F);
         hlb = fadd(hlb, fmul(qlb[c], dq[c], F), F);
         hrb = fadd(hrb, fmul(-qrb[c], dq[c], F), F);
-        qb[1][c] = fadd(qb[1][c], fadd(qlb[c], -dqb, F), F);
-        qb[2][c] = fadd(qb[2][c], fadd(qrb[c], dqb, F), F);
+        qb[0][c] = fadd(qlb[c], -dqb, F);
+        qb[1][c] = fadd(qrb[c], dqb, F);
     }
     // pressures: hl from (p1 - p0, p2 - p1), hr from (p2 - p1, p3 - p2)
-    double pb[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        pb[m] = 0.0;
     const double a1 = fmul(hlb, dl_dm, F), a2 = fmul(hlb, dl_dp, F);
     pb[1] = fadd(pb[1], a1, F);
     pb[0] = fadd(pb[0], -a1, F);
@@ -233,9 +235,6 @@ __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q
     pb[1] = fadd(pb[1], -b1, F);
     pb[3] = fadd(pb[3], b2, F);
     pb[2] = fadd(pb[2], -b2, F);
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-        cell_pressure_vjp(mn[m], mt[m], inv[m], un[m], ut[m], k, pb[m], qb[m]);
 }
 
 // Per cell: cp[0..3][cell] = pressure, 1/rho, u, v (the arithmetic of
@@ -290,20 +289,20 @@ __global__ void __launch_bounds__(kThreads) k_vjp_limiters(Params p, const doubl
 }
 
 // Per face (axis 0: between (i,j) and (i+1,j); axis 1: between (i,j) and
-// (i,j+1)): the contributions of <v_right - v_left, Fh(Q)> to the gradient of
-// the four cells of its line.  fo[(axis*16 + m*4 + c) * plane + j*nx + i],
-// cell m = 0..3 at offset m-1 along the axis, component c in the
-// (rho, m_x, m_y, E) order.  cp, lp: k_vjp_cells and k_vjp_limiters of q.
-// 128-thread CTAs held to 128 registers: four CTAs (16 warps) per SM, where
-// the 138 registers the compiler would otherwise take leave room for one
-// 256-thread CTA (8 warps) to hide the long divide and square-root chains.
+// (i,j+1)): the contributions of <v_right - v_left, Fh(Q)>.  Layout
+// fo[(axis*12 + t) * plane + j*nx + i]: t = 0..3 the gradient for the
+// face's left cell (cell 1 of its line), t = 4..7 for its right cell (cell
+// 2), components in the (rho, m_x, m_y, E) order; t = 8..11 the pressure
+// adjoints of cells 0..3 of its line (offsets -1..2 along the axis).
+// lp: k_vjp_limiters of q.  128-thread CTAs held to 128 registers: four
+// CTAs (16 warps) per SM to hide the long divide and square-root chains.
 #ifndef SWEEP_VJP_THREADS
 #define SWEEP_VJP_THREADS 128
 #endif
 constexpr int kVjpThreads = SWEEP_VJP_THREADS;
+constexpr int kFacePlanes = 12;  // per axis
 __global__ void __launch_bounds__(kVjpThreads, 512 / kVjpThreads)
-    k_face_vjp(Params p, const double *q, const double *cp, const double *lp, const double *v,
-               double *fo)
+    k_face_vjp(Params p, const double *q, const double *lp, const double *v, double *fo)
 {
     const int64_t plane = p.nx * p.ny;
     const Fx F = p.ek.f;
@@ -315,53 +314,48 @@ __global__ void __launch_bounds__(kVjpThreads, 512 / kVjpThreads)
     const int64_t i = cell % p.nx, j = cell / p.nx;
     // normal-frame component order: (rho, m_n, m_t, E)
     const int c1 = axis == 0 ? 1 : 2, c2 = axis == 0 ? 2 : 1;
-    int64_t idx[4];
-    double mn[4], mt[4], inv[4], un[4], ut[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        int64_t ii = i, jj = j;
-        if (axis == 0) {
-            ii = i - 1 + m;
-            ii = ii < 0 ? ii + p.nx : (ii >= p.nx ? ii - p.nx : ii);
-        } else {
-            jj = j - 1 + m;
-            jj = jj < 0 ? jj + p.ny : (jj >= p.ny ? jj - p.ny : jj);
-        }
-        idx[m] = jj * p.nx + ii;
-        mn[m] = q[c1 * plane + idx[m]];
-        mt[m] = q[c2 * plane + idx[m]];
-        inv[m] = cp[plane + idx[m]];
-        un[m] = cp[(1 + c1) * plane + idx[m]];
-        ut[m] = cp[(1 + c2) * plane + idx[m]];
-    }
-    const double q1[4] = {q[idx[1]], mn[1], mt[1], q[3 * plane + idx[1]]};
-    const double q2[4] = {q[idx[2]], mn[2], mt[2], q[3 * plane + idx[2]]};
+    // cells 1 and 2 of the line: this cell and its + neighbour
+    int64_t right;
+    if (axis == 0)
+        right = j * p.nx + (i + 1 == p.nx ? 0 : i + 1);
+    else
+        right = (j + 1 == p.ny ? 0 : j + 1) * p.nx + i;
+    const double q1[4] = {q[cell], q[c1 * plane + cell], q[c2 * plane + cell], q[3 * plane + cell]};
+    const double q2[4] = {q[right], q[c1 * plane + right], q[c2 * plane + right],
+                          q[3 * plane + right]};
     const double *L = lp + (int64_t)axis * 6 * plane;
-    const double lim1[3] = {L[idx[1]], L[plane + idx[1]], L[2 * plane + idx[1]]};
-    const double lim2[3] = {L[3 * plane + idx[2]], L[4 * plane + idx[2]], L[5 * plane + idx[2]]};
-    const double a[4] = {fadd(v[idx[2]], -v[idx[1]], F),
-                         fadd(v[c1 * plane + idx[2]], -v[c1 * plane + idx[1]], F),
-                         fadd(v[c2 * plane + idx[2]], -v[c2 * plane + idx[1]], F),
-                         fadd(v[3 * plane + idx[2]], -v[3 * plane + idx[1]], F)};
-    double qb[4][4];
-    face_flux_vjp(q1, q2, mn, mt, inv, un, ut, lim1, lim2, a, p.ek, qb);
-    double *o = fo + (int64_t)axis * 16 * plane + cell;
+    const double lim1[3] = {L[cell], L[plane + cell], L[2 * plane + cell]};
+    const double lim2[3] = {L[3 * plane + right], L[4 * plane + right], L[5 * plane + right]};
+    const double a[4] = {fadd(v[right], -v[cell], F),
+                         fadd(v[c1 * plane + right], -v[c1 * plane + cell], F),
+                         fadd(v[c2 * plane + right], -v[c2 * plane + cell], F),
+                         fadd(v[3 * plane + right], -v[3 * plane + cell], F)};
+    double qb[2][4], pb[4];
+    face_flux_vjp(q1, q2, lim1, lim2, a, p.ek, qb, pb);
+    double *o = fo + (int64_t)axis * kFacePlanes * plane + cell;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < 2; ++m) {
         o[(m * 4 + 0) * plane] = qb[m][0];
         o[(m * 4 + c1) * plane] = qb[m][1];
         o[(m * 4 + c2) * plane] = qb[m][2];
         o[(m * 4 + 3) * plane] = qb[m][3];
     }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        o[(8 + m) * plane] = pb[m];
 }
 
-// Per cell: S = J^T v at the cell, summed from its eight faces in a fixed
-// order (x faces, then y faces; along each axis the faces in increasing
-// wrapped index), then
+// Per cell: S = J^T v at the cell.  The face at index e along an axis
+// reaches this cell as cell m of its line, e = pos + 1 - m (wrapped); the
+// faces are summed in increasing e, x faces then y faces: the gradients
+// through the reconstructed states (m = 1, 2) into S, the pressure adjoints
+// (m = 0..3) into pb; then S takes the reverse of the cell's pressure for
+// pb (q, cp: the state and its k_vjp_cells terms), and
 //   mode 0:  mu = lam2 S                 (mu: out)
 //   mode 1:  lam = (lam + mu) + lam1 S   (lam: in place)
-__global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo, double *lam,
-                                                     double *mu, int mode)
+__global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo, const double *q,
+                                                     const double *cp, double *lam, double *mu,
+                                                     int mode)
 {
     const int64_t plane = p.nx * p.ny;
     const Fx F = p.ek.f;
@@ -369,8 +363,6 @@ __global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo,
     if (cell >= plane)
         return;
     const int64_t i = cell % p.nx, j = cell / p.nx;
-    // the face at index e along an axis reaches this cell as its cell m with
-    // e = (pos + 1 - m) wrapped; visit the four faces in increasing e
     int64_t ex[4], ey[4];
     int mx[4], my[4];
 #pragma unroll
@@ -403,20 +395,37 @@ __global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo,
             my[t] = my[t - 1];
             my[t - 1] = tm;
         }
+    const double *fx = fo, *fy = fo + (int64_t)kFacePlanes * plane;
+    double S[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         double s = 0.0;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-            s = fadd(s, fo[(int64_t)(0 * 16 + mx[t] * 4 + c) * plane + j * p.nx + ex[t]], F);
+            if (mx[t] == 1 || mx[t] == 2)
+                s = fadd(s, fx[(int64_t)((mx[t] - 1) * 4 + c) * plane + j * p.nx + ex[t]], F);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-            s = fadd(s, fo[(int64_t)(1 * 16 + my[t] * 4 + c) * plane + ey[t] * p.nx + i], F);
+            if (my[t] == 1 || my[t] == 2)
+                s = fadd(s, fy[(int64_t)((my[t] - 1) * 4 + c) * plane + ey[t] * p.nx + i], F);
+        S[c] = s;
+    }
+    double pb = 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        pb = fadd(pb, fx[(int64_t)(8 + mx[t]) * plane + j * p.nx + ex[t]], F);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        pb = fadd(pb, fy[(int64_t)(8 + my[t]) * plane + ey[t] * p.nx + i], F);
+    cell_pressure_vjp(q[plane + cell], q[2 * plane + cell], cp[plane + cell], cp[2 * plane + cell],
+                      cp[3 * plane + cell], p.ek, pb, S);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
         const int64_t o = c * plane + cell;
         if (mode == 0)
-            mu[o] = fmul(p.c2, s, F);
+            mu[o] = fmul(p.c2, S[c], F);
         else
-            lam[o] = fadd(fadd(lam[o], mu[o], F), fmul(p.c1, s, F), F);
+            lam[o] = fadd(fadd(lam[o], mu[o], F), fmul(p.c1, S[c], F), F);
     }
 }
 

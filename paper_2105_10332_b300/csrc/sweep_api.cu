@@ -319,7 +319,7 @@ AdjLayout adjoint_layout(const sweep_s *h, int64_t nsteps, int64_t ckpt)
     L.lp = off;
     off += (plane * 12 + 255) / 256 * 256;
     L.faces = off;
-    off += plane * 32;
+    off += plane * 2 * kFacePlanes;
     L.total = off;
     return L;
 }
@@ -372,12 +372,12 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
         for (int64_t t = len - 1; t >= 0; --t) {
             k_vjp_cells<<<gc, kThreads, 0, st>>>(p, qs_ptr(t), cp);
             k_vjp_limiters<<<gc, kThreads, 0, st>>>(p, cp, lp);
-            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, qs_ptr(t), cp, lp, lam0, faces);
-            k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 0);
+            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, qs_ptr(t), lp, lam0, faces);
+            k_gather<<<gc, kThreads, 0, st>>>(p, faces, qs_ptr(t), cp, lam0, mu, 0);
             k_vjp_cells<<<gc, kThreads, 0, st>>>(p, seg_ptr(t), cp);
             k_vjp_limiters<<<gc, kThreads, 0, st>>>(p, cp, lp);
-            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, seg_ptr(t), cp, lp, mu, faces);
-            k_gather<<<gc, kThreads, 0, st>>>(p, faces, lam0, mu, 1);
+            k_face_vjp<<<gf, kVjpThreads, 0, st>>>(p, seg_ptr(t), lp, mu, faces);
+            k_gather<<<gc, kThreads, 0, st>>>(p, faces, seg_ptr(t), cp, lam0, mu, 1);
         }
         if (cudaGetLastError() != cudaSuccess) return SWEEP_ECUDA;
     }

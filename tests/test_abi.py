@@ -91,10 +91,11 @@ def test_adjoint_workspace_and_argument_checks(L):
     slot = (4 * 64 * 64 * 8 + 255) // 256 * 256
     # level store (7 slots) + 32 checkpoints + 64-step segment + its 64 first
     # stages Q* + mu* + per-cell pressure terms (4) + limiter terms (12) + faces
+    # (per axis: 8 state gradients and 4 pressure adjoints)
     nseg = (2000 + 63) // 64
     plane = 64 * 64 * 8
     expect = (256 + slot * 7 + slot * nseg + slot * 64 + slot * 64 + slot + 4 * plane
-              + 12 * plane + 32 * plane)
+              + 12 * plane + 24 * plane)
     assert S.sweep_adjoint_workspace_bytes(h, 2000, 64) == expect
     assert S.sweep_adjoint_workspace_bytes(h, 2000, 0) == 0
     p = ctypes.c_void_p(4096)
