@@ -88,6 +88,14 @@ struct Params {
     double *ws;          // level store: d+1 slots
     int64_t slot_elems;  // doubles per slot (>= ncomp*nx*ny, padded)
     int passes;          // row bands each CTA takes one after another per level
+    // Level history (the adjoint's swept recompute, equation EulerHist):
+    // every level l < hist_levels that a kernel computes is also written to
+    // the full-grid state array of its level: level 2t (Q^t) at
+    // hist_q + t*hist_stride, level 2t+1 (the first stage Q*_t) at
+    // hist_qs + t*hist_stride.  Each (cell, level) is computed exactly once
+    // in a swept run, so the arrays end up complete.
+    double *hist_q, *hist_qs;
+    int64_t hist_stride, hist_levels;
 };
 
 // ------------------------------------------------------------------ equations
@@ -97,6 +105,13 @@ struct Heat {
     static constexpr int N = 1;
 };
 struct Euler {
+    static constexpr int NC = 4;
+    static constexpr int N = 2;
+};
+// The same Euler scheme, each computed level also written to the level
+// history of Params (the adjoint's swept recompute); a distinct type so that
+// the forward kernels carry no trace of it.
+struct EulerHist {
     static constexpr int NC = 4;
     static constexpr int N = 2;
 };
@@ -355,9 +370,9 @@ struct Stage<HeatFE, C> {
     }
 };
 
-template <int C>
-struct Stage<Euler, C> {
-    __device__ static void run(const Params &p, Block<Euler, C> &B, int64_t level, Rect R)
+template <class EQ, int C, bool HIST>
+struct EulerStage {
+    __device__ static void run(const Params &p, Block<EQ, C> &B, int64_t level, Rect R)
     {
         const int np = B.bands / C;
         for (int k = 0; k < np; ++k) {
@@ -365,7 +380,7 @@ struct Stage<Euler, C> {
             run_band(p, B, level, band(R, B.rank * np + k, B.bands));
         }
     }
-    __device__ static void run_band(const Params &p, Block<Euler, C> &B, int64_t level, Rect S)
+    __device__ static void run_band(const Params &p, Block<EQ, C> &B, int64_t level, Rect S)
     {
         const bool second = (level & 1) == 0;
         const double *src = B.buf[(level - 1) & 1];
@@ -496,22 +511,43 @@ struct Stage<Euler, C> {
         }
         __syncthreads();
         // (d) conservative update of S, written to every CTA of the cluster
+        //     (and to the level history, where one is recorded)
         if (!idle) {
+            double *hist = nullptr;
+            if constexpr (HIST) {
+                if (level < p.hist_levels)
+                    hist = (level & 1) ? p.hist_qs + ((level - 1) >> 1) * p.hist_stride
+                                       : p.hist_q + (level >> 1) * p.hist_stride;
+            }
+            const int64_t gplane = p.nx * p.ny;
             for_rect(S, [&](int x, int y) {
                 const int i = y * wp + x;
                 const int xo = x - S.x0, yo = y - S.y0;
                 const int ofx = yo * fxw + xo;  // face at x - 1/2
                 const int ofy = yo * W + xo;    // face at y - 1/2
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    B.put(level, c, i,
-                          euler_combine(B.fx[c * fxpl + ofx], B.fx[c * fxpl + ofx + 1],
-                                        B.fy[c * fypl + ofy], B.fy[c * fypl + ofy + W],
-                                        own[c * pl + i], lam, k.f));
+                for (int c = 0; c < 4; ++c) {
+                    const double v =
+                        euler_combine(B.fx[c * fxpl + ofx], B.fx[c * fxpl + ofx + 1],
+                                      B.fy[c * fypl + ofy], B.fy[c * fypl + ofy + W],
+                                      own[c * pl + i], lam, k.f);
+                    B.put(level, c, i, v);
+                    if constexpr (HIST) {
+                        if (hist) hist[c * gplane + gidx(p, B.ox, B.oy, x, y)] = v;
+                    }
+                }
             });
+            (void)hist;
+            (void)gplane;
         }
     }
 };
+
+template <int C>
+struct Stage<Euler, C> : EulerStage<Euler, C, false> {};
+
+template <int C>
+struct Stage<EulerHist, C> : EulerStage<EulerHist, C, true> {};
 
 // -------------------------------------------------------------- shape engines
 

@@ -100,6 +100,10 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     p.ws = ws ? (double *)((char *)ws + kHeader) : nullptr;
     p.slot_elems = slot_elems(h);
     p.passes = h->passes;
+    p.hist_q = nullptr;
+    p.hist_qs = nullptr;
+    p.hist_stride = 0;
+    p.hist_levels = 0;
     return p;
 }
 
@@ -364,9 +368,25 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
         if (cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess)
             return SWEEP_ECUDA;
-        // recompute the segment, keeping each step's first stage Q*; the
-        // last step's end state is not needed and lands in mu (unused yet)
-        for (int64_t t = 0; t < len; ++t)
+        // recompute the segment swept-wise from its checkpoint, recording
+        // every level: Q^t in seg_ptr(t), the first stages Q*_t in
+        // qs_ptr(t); mu (unused yet) holds the running state.  The steps
+        // left after the last whole swept cycle are Standard steps that
+        // write Q*_t as well; the last step's end state is not needed and
+        // lands in mu.
+        const int64_t swept_levels = 2 * len >= h->depth ? (2 * len / h->depth) * h->depth : 0;
+        if (swept_levels > 0) {
+            if (cudaMemcpyAsync(mu, seg_ptr(0), sbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return SWEEP_ECUDA;
+            Params ph = make_params(h, mu, ws);
+            ph.hist_q = seg_ptr(0);
+            ph.hist_qs = qs_ptr(0);
+            ph.hist_stride = (int64_t)(sstride / sizeof(double));
+            ph.hist_levels = 2 * len;
+            const int rc = swept<EulerHist>(h, ph, swept_levels, st);
+            if (rc != SWEEP_OK) return rc;
+        }
+        for (int64_t t = swept_levels / 2; t < len; ++t)
             k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(
                 p, seg_ptr(t), t + 1 < len ? seg_ptr(t + 1) : mu, qs_ptr(t));
         for (int64_t t = len - 1; t >= 0; --t) {
