@@ -467,11 +467,10 @@ struct EulerStage {
         const int fxpl = rows * (wp - 3);        // x-flux component plane
         const int fypl = (rows + 1) * (wp - 4);  // y-flux component plane
         if (!idle) {
-            const int total = nfx + nfy;
-            for (int q = threadIdx.x; q < total; q += blockDim.x) {
-                int i0, st, ca, cb, opl;
-                const double *hl, *hr;
-                double *out;
+            // face q: its left cell's index, the stride to the right cell,
+            // the frame's component order, the limiter halves and the output
+            auto face = [&](int q, int &i0, int &st, int &ca, int &cb, int &opl, const double *&hl,
+                            const double *&hr, double *&out) {
                 if (q < nfx) {
                     const int fo = q % fxw, yo = q / fxw;
                     const int x = S.x0 + fo, y = S.y0 + yo;
@@ -498,6 +497,20 @@ struct EulerStage {
                     out = B.fy + go * W + xo;
                     opl = fypl;
                 }
+            };
+            // Faces past the last whole group of 128 (one warp per SM
+            // sub-partition) cost a whole face's FP64 issue time however few
+            // they are.  When at most 64 are left they go two lanes per face
+            // (face_flux_half), onto the warps after the last full pass.
+            const int total = nfx + nfy;
+            const int rem = total & 127;
+            const int nsplit = (rem != 0 && rem <= 64) ? rem : 0;
+            const int nnorm = total - nsplit;
+            for (int q = threadIdx.x; q < nnorm; q += blockDim.x) {
+                int i0, st, ca, cb, opl;
+                const double *hl, *hr;
+                double *out;
+                face(q, i0, st, ca, cb, opl, hl, hr, out);
                 const int i1 = i0 + st;
                 const double q0[4] = {src[i0], src[ca * pl + i0], src[cb * pl + i0], src[3 * pl + i0]};
                 const double q1[4] = {src[i1], src[ca * pl + i1], src[cb * pl + i1], src[3 * pl + i1]};
@@ -507,6 +520,29 @@ struct EulerStage {
                 out[ca * opl] = fh[1];
                 out[cb * opl] = fh[2];
                 out[3 * opl] = fh[3];
+            }
+            if (nsplit) {
+                // nnorm is a multiple of 128: the lanes start at a warp
+                // boundary, after the threads of the last normal pass
+                const int l = (int)threadIdx.x - (int)(nnorm % blockDim.x);
+                const bool part = l >= 0 && l < 2 * nsplit;
+                const unsigned mask = __ballot_sync(0xffffffffu, part);
+                if (part) {
+                    int i0, st, ca, cb, opl;
+                    const double *hl, *hr;
+                    double *out;
+                    face(nnorm + (l >> 1), i0, st, ca, cb, opl, hl, hr, out);
+                    const int i1 = i0 + st;
+                    const double q0[4] = {src[i0], src[ca * pl + i0], src[cb * pl + i0],
+                                          src[3 * pl + i0]};
+                    const double q1[4] = {src[i1], src[ca * pl + i1], src[cb * pl + i1],
+                                          src[3 * pl + i1]};
+                    const int side = l & 1;
+                    double fa, fb;
+                    face_flux_half(q0, q1, *hl, *hr, side, mask, k, fa, fb);
+                    out[(side ? cb : 0) * opl] = fa;
+                    out[(side ? 3 : ca) * opl] = fb;
+                }
             }
         }
         __syncthreads();

@@ -171,6 +171,44 @@ __device__ __forceinline__ void face_flux(const double q0[4], const double q1[4]
         fh[c] = fmul(0.5, __fma_rn(r, fadd(ql[c], -qr[c], x), fadd(fl[c], fr[c], x)), x);
 }
 
+// face_flux taken by the two lanes of a pair (lanes 2k and 2k+1 of a warp,
+// side = lane & 1): side 0 reconstructs Q_L and returns components 0 and 1
+// of Fh in fa, fb; side 1 reconstructs Q_R and returns components 2 and 3.
+// Each lane computes one state flux and hands its partner, by shuffle, the
+// state and flux components the partner returns; every component takes
+// face_flux's operations in face_flux's order, so the bits are the same.
+// mask: the lanes taking part (both lanes of every pair).
+__device__ __forceinline__ void face_flux_half(const double q0[4], const double q1[4], double hl,
+                                               double hr, int side, unsigned mask,
+                                               const EulerConst &k, double &fa, double &fb)
+{
+    const Fx &x = k.f;
+    const double h = side ? -hr : hl;
+    double st[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double dq = fadd(q1[c], -q0[c], x);
+        st[c] = __fma_rn(h, dq, side ? q1[c] : q0[c]);
+    }
+    double f[4], lam;
+    state_flux(st[0], st[1], st[2], st[3], k, f, lam);
+    // the partner's state and flux for the two components this lane returns
+    const double pq0 = __shfl_xor_sync(mask, side ? st[0] : st[2], 1);
+    const double pq1 = __shfl_xor_sync(mask, side ? st[1] : st[3], 1);
+    const double pf0 = __shfl_xor_sync(mask, side ? f[0] : f[2], 1);
+    const double pf1 = __shfl_xor_sync(mask, side ? f[1] : f[3], 1);
+    const double plam = __shfl_xor_sync(mask, lam, 1);
+    const double r = side ? max_nonneg(plam, lam) : max_nonneg(lam, plam);
+    const double m0 = side ? st[2] : st[0], m1 = side ? st[3] : st[1];
+    const double g0 = side ? f[2] : f[0], g1 = side ? f[3] : f[1];
+    const double ql0 = side ? pq0 : m0, qr0 = side ? m0 : pq0;
+    const double ql1 = side ? pq1 : m1, qr1 = side ? m1 : pq1;
+    const double fl0 = side ? pf0 : g0, fr0 = side ? g0 : pf0;
+    const double fl1 = side ? pf1 : g1, fr1 = side ? g1 : pf1;
+    fa = fmul(0.5, __fma_rn(r, fadd(ql0, -qr0, x), fadd(fl0, fr0, x)), x);
+    fb = fmul(0.5, __fma_rn(r, fadd(ql1, -qr1, x), fadd(fl1, fr1, x)), x);
+}
+
 // out = fma(lam, (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2} - Gh_{j+1/2}), own)
 __device__ __forceinline__ double euler_combine(double fm, double fp, double gm, double gp,
                                                 double own, double lam, const Fx &f)
