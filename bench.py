@@ -42,11 +42,13 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands (profiles/); an entry is removed whenever that kernel changes.  The
-# 16384^2 heat Octahedron has none: at 4096^2 its reads of the Bridges'
-# exports hit L2 (1.5 of 448 MB), at 16384^2 the exports (16x) cannot, so the
-# smaller capture does not scale in proportion.
-TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9246720 + 0,
-                      ("heat_modes_4096x4096_200steps", "octahedron"): 1519754 + 445980672}
+# 16384^2 heat Octahedron is too large to capture under the profiling size
+# rule: its entry is the 4096^2 capture scaled by the 16x windows, since at
+# both sizes the state and the level store are far larger than L2.
+HEAT4096_OCT_TRAFFIC = 1519322368 + 445884672
+TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 9261056 + 0,
+                      ("heat_modes_4096x4096_200steps", "octahedron"): HEAT4096_OCT_TRAFFIC,
+                      ("heat_modes_16384x16384_2000steps", "octahedron"): 16 * HEAT4096_OCT_TRAFFIC}
 
 
 def workload(name):
