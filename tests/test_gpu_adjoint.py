@@ -128,8 +128,8 @@ def test_autograd_function(torch_cuda, oracle_lib):
     assert relerr(q.grad.cpu().numpy(), ref) <= 1e-12
 
 
-def test_euler_adjoint_config4_full_size(torch_cuda):
-    """Config 4 at its full size, as bench.py runs it (1024^2 vortex, 2000
+def test_euler_adjoint_1024_full_size(torch_cuda):
+    """The 1024^2 vortex adjoint at its full size, as bench.py runs it (2000
     steps, checkpoints every 64, unlimited reconstruction, loss
     sum((rho_T - rho_target)^2)): the gradient against central differences of
     the GPU forward solver along 3 seeded directions, h = 1e-6 (measured

@@ -59,7 +59,7 @@ def euler_solver(S, nx, ny, tile, depth, T=1.0, **kw):
 
 # ------------------------------------------------------------------- heat
 
-def test_heat_standard_matches_oracle_config1(torch_cuda, oracle_lib):
+def test_heat_standard_matches_oracle_sine64(torch_cuda, oracle_lib):
     from paper_2105_10332_b300 import sweep as S
     s, r = heat_solver(S, 64, 64, 16, 6)
     u0 = W.heat_sine(64, 64)
@@ -88,8 +88,8 @@ def test_heat_swept_bit_identical(torch_cuda, oracle_lib, nx, ny, tile, nsteps):
         assert np.array_equal(sw, std), ("d=%d" % d, relerr(sw, std))
 
 
-def test_heat_swept_config1_and_closed_form(torch_cuda, oracle_lib):
-    """Config 1 (64^2, r = 0.1, 500 steps, tile 16): Swept = Standard = oracle,
+def test_heat_swept_sine64_and_closed_form(torch_cuda, oracle_lib):
+    """Heat sine 64^2, r = 0.1, 500 steps, tile 16: Swept = Standard = oracle,
     and the discrete closed form G^500 within 1e-13."""
     from paper_2105_10332_b300 import sweep as S
     s, r = heat_solver(S, 64, 64, 16, 6)
@@ -171,8 +171,8 @@ def test_resume_is_bit_identical(torch_cuda):
 
 # ------------------------------------------------------------------- full sizes
 
-def test_euler_config2_full_run(torch_cuda, oracle_lib):
-    """Config 2: vortex 256^2, CFL 0.25, t = 10 (2999 steps), tile 32, d = 6 --
+def test_euler_vortex256_full_run(torch_cuda, oracle_lib):
+    """Vortex 256^2, CFL 0.25, t = 10 (2999 steps), tile 32, d = 6 --
     the launch configuration the benchmark times.  Swept = Standard bitwise,
     and both equal the oracle's full run."""
     from paper_2105_10332_b300 import sweep as S
@@ -193,7 +193,7 @@ def test_euler_config2_full_run(torch_cuda, oracle_lib):
 
 
 def test_heat_large_sampled_closed_form(torch_cuda):
-    """Config 3 shape (seeded 8-mode field, r = 0.1) at 4096^2 for 200 steps:
+    """The seeded 8-mode heat field (r = 0.1) at 4096^2 for 200 steps:
     Swept = Standard bitwise and sampled cells match the discrete closed form."""
     from paper_2105_10332_b300 import sweep as S
     torch = torch_cuda
@@ -254,9 +254,9 @@ def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, passes, eq
             assert np.array_equal(got, ref), (cluster, d, N, relerr(got, ref))
 
 
-def test_heat_config3_full_size(torch_cuda):
-    """Config 3 at its full size and in the launch configuration bench.py
-    times (16384^2, 2000 steps, block 64, depth 30): Swept = Standard
+def test_heat_modes16384_full_size(torch_cuda):
+    """Heat 16384^2 at its full size and in the launch configuration
+    bench.py times (2000 steps, block 64, depth 30): Swept = Standard
     bitwise, and 256 sampled cells match the discrete closed form
     (measured gap 5.5e-14 of max|u0|)."""
     from paper_2105_10332_b300 import sweep as S

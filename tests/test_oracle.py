@@ -27,7 +27,7 @@ def heat_growth(kx, ky, nx, ny, r, scheme):
 
 
 def test_heat_closed_form_sine_64(oracle_lib):
-    """Config 1: 64^2, r = 0.1, 500 RK2 steps of T0 = sin 2pi x sin 2pi y (App. A)."""
+    """Heat 64^2, r = 0.1, 500 RK2 steps of T0 = sin 2pi x sin 2pi y (App. A)."""
     u0 = W.heat_sine(64, 64)
     u = oracle_lib.heat_run(u0, 0.1, 500)
     G = heat_growth(1, 1, 64, 64, 0.1, 0)
