@@ -150,11 +150,15 @@ int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
  *          through the swept kernels.  d_q0 is not read (may be NULL);
  *          d_lam0 may equal d_lamT.
  *   Euler: a forward swept pass from d_q0 keeps a checkpoint every
- *          ckpt_every steps; each segment is then recomputed one Standard
- *          step at a time, keeping every step's first stage, and reversed
- *          step by step (face-wise reverse mode of the flux, gathered per
- *          cell; the terms that neighbouring faces share are computed once
- *          per cell).  d_lam0 must not alias d_lamT.
+ *          ckpt_every steps; each segment is then recomputed by one swept
+ *          run from its checkpoint that records every step's state and
+ *          first stage (the steps after its last whole swept cycle are
+ *          Standard steps), and reversed step by step: face-wise reverse
+ *          mode of the flux, gathered per cell in a fixed order (x faces,
+ *          then y faces, in increasing face index); the terms that
+ *          neighbouring faces share, and the reverse of each cell's
+ *          pressure, are computed once per cell.  d_lam0 must not alias
+ *          d_lamT.
  * d_ws: sweep_adjoint_workspace_bytes(h, nsteps, ckpt_every) bytes,
  * 256-byte aligned.  Asynchronous on the stream like the other runs.
  */
