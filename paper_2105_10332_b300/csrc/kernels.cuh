@@ -370,6 +370,10 @@ struct Stage<HeatFE, C> {
     }
 };
 
+// One Euler stage (App. B) over this CTA's band of a region: cell
+// pressures, half limiter factors, face fluxes, conservative update.  EQ is
+// Euler or EulerHist; HIST (EulerHist) also writes every computed level to
+// the level history of Params.
 template <class EQ, int C, bool HIST>
 struct EulerStage {
     __device__ static void run(const Params &p, Block<EQ, C> &B, int64_t level, Rect R)
