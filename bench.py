@@ -39,6 +39,16 @@ FLOPS_PER_CELL_STAGE = {"heat": 7, "euler": 187}
 # FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA lanes per clock
 # (measured: 565 G FMA/s at 1.94 GHz) x 2 flops x 2032 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+HBM_FALLBACK_GBS = 6400.0  # used only where no measured copy bandwidth is on file
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the B300s (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands (profiles/); an entry is removed whenever that kernel changes.  The
@@ -499,12 +509,20 @@ def run_ours(args, wl):
         dom_cells = shape_cells(wl["eqn"], wl["tile"], wl["depth"], dom, tiles)
     flops = dom_cells * FLOPS_PER_CELL_STAGE[wl["eqn"]]
     achieved = flops / (dom_ms / 1e3) / 1e12
+    traffic = TRAFFIC_PER_LAUNCH.get((wl["name"], dom))
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": TRAFFIC_PER_LAUNCH.get((wl["name"], dom)),
+                "traffic": traffic,
                 "kernel": dom, "launch_ms": round(dom_ms, 5),
                 "flops_per_launch": flops, "peak_basis": "FP64 148 SMs x 2 FMA/clk x 2032 MHz (derived)",
                 "kernels": {k: {"ms_total": round(v[0], 4), "launches": v[1]} for k, v in prof.items()}}
+    # the HBM side of the same kernel: its ncu DRAM bytes per launch over the
+    # live launch time, against the copy bandwidth
+    if traffic is not None:
+        peak_gbs, basis = hbm_peak_gbs()
+        gbs = traffic / (dom_ms / 1e3) / 1e9
+        roofline["hbm"] = {"achieved": round(gbs, 2), "peak": peak_gbs, "unit": "GB/s",
+                           "frac": round(gbs / peak_gbs, 4), "peak_basis": basis}
 
     line = None
     if rank == 0:
