@@ -194,14 +194,17 @@ __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q
     const bool left = __double_as_longlong(laml) > __double_as_longlong(lamr);
     const double r = left ? laml : lamr;
     // Fh_c = 1/2 (r (ql_c - qr_c) + fl_c + fr_c)
+    // (-r/2) a rounds to exactly -((r/2) a), signed zeros included (round
+    // to nearest is symmetric), so qrb starts as the negation of qlb
     double qlb[4], qrb[4], flb[4], frb[4], rb = 0.0;
+    const double half_r = fmul(0.5, r, F);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         flb[c] = fmul(0.5, a[c], F);
         frb[c] = flb[c];
-        qlb[c] = fmul(fmul(0.5, r, F), a[c], F);
-        qrb[c] = fmul(fmul(-0.5, r, F), a[c], F);
-        rb = fadd(rb, fmul(fmul(0.5, a[c], F), fadd(ql[c], -qr[c], F), F), F);
+        qlb[c] = fmul(half_r, a[c], F);
+        qrb[c] = -qlb[c];
+        rb = fadd(rb, fmul(flb[c], fadd(ql[c], -qr[c], F), F), F);
     }
     // r = lam of one state: only that state's sound speed carries rb
     const double cm = left ? pl.c : pr.c;

@@ -284,6 +284,22 @@ __device__ __forceinline__ double *slot_ptr(const Params &p, int64_t level)
     return p.ws + (level % (p.d + 1)) * p.slot_elems;
 }
 
+// Index of the window cell (x, y) of the window at (ox, oy) inside one
+// component plane of a level-store slot.  The store keeps each 2 x 2 block
+// of cells together (32 bytes: one DRAM sector), blocks row-major, so that
+// the thin column pieces of the frames and rings that shapes hand over fill
+// whole sectors; a row-major store would fetch and write a sector for every
+// 8 or 16 bytes of such a column.  nx and ny are even.
+__device__ __forceinline__ int64_t sidx(const Params &p, int64_t ox, int64_t oy, int x, int y)
+{
+    int64_t gx = ox + x, gy = oy + y;
+    if (gx < 0) gx += p.nx;
+    if (gx >= p.nx) gx -= p.nx;
+    if (gy < 0) gy += p.ny;
+    if (gy >= p.ny) gy -= p.ny;
+    return (((gy >> 1) * (p.nx >> 1) + (gx >> 1)) << 2) + ((gy & 1) << 1) + (gx & 1);
+}
+
 // 8-byte asynchronous global -> shared copy (cp.async), and the wait for all
 // of this thread's outstanding copies
 __device__ __forceinline__ void cp_async8(double *smem_dst, const double *gsrc)
@@ -305,7 +321,7 @@ __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &
     double *dst = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
     for_diff(O, I, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
+        const int64_t g = sidx(p, B.ox, B.oy, x, y);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
             cp_async8(dst + c * B.plane + y * B.wp + x, src + c * gplane + g);
@@ -320,7 +336,7 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
     const double *src = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
     for_diff(O, I, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
+        const int64_t g = sidx(p, B.ox, B.oy, x, y);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
             dst[c * gplane + g] = src[c * B.plane + y * B.wp + x];
