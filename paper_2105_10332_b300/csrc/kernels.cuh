@@ -290,9 +290,14 @@ __device__ __forceinline__ double *slot_ptr(const Params &p, int64_t level)
 // the thin column pieces of the frames and rings that shapes hand over fill
 // whole sectors; a row-major store would fetch and write a sector for every
 // 8 or 16 bytes of such a column.  nx and ny are even.
-__device__ __forceinline__ int64_t sidx(const Params &p, int64_t ox, int64_t oy, int x, int y)
+// The pieces are 2n cells thick.  For n = 2 they start on even coordinates
+// at every level; for n = 1 a piece of level l starts on coordinates of l's
+// parity (d and b/2 even), so odd levels of a one-cell-radius equation shift
+// the block grid by one cell (shift = 1) to keep the pieces block-aligned.
+__device__ __forceinline__ int64_t sidx(const Params &p, int64_t ox, int64_t oy, int x, int y,
+                                        int shift)
 {
-    int64_t gx = ox + x, gy = oy + y;
+    int64_t gx = ox + x + shift, gy = oy + y + shift;
     if (gx < 0) gx += p.nx;
     if (gx >= p.nx) gx -= p.nx;
     if (gy < 0) gy += p.ny;
@@ -320,8 +325,9 @@ __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &
     const double *src = slot_ptr(p, level);
     double *dst = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
+    const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     for_diff(O, I, [&](int x, int y) {
-        const int64_t g = sidx(p, B.ox, B.oy, x, y);
+        const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
             cp_async8(dst + c * B.plane + y * B.wp + x, src + c * gplane + g);
@@ -335,8 +341,9 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
     double *dst = slot_ptr(p, level);
     const double *src = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
+    const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     for_diff(O, I, [&](int x, int y) {
-        const int64_t g = sidx(p, B.ox, B.oy, x, y);
+        const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
             dst[c * gplane + g] = src[c * B.plane + y * B.wp + x];
