@@ -93,9 +93,10 @@ int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile
  *   "cluster"        CTAs sharing one swept window through distributed shared
  *                    memory, for every swept kernel (1, 2, 4); "cluster_oct"
  *                    and "cluster_bridges" set the Up-Pyramid/Octahedron and
- *                    the Bridge kernels separately.  Defaults: Euler 2 and 1,
- *                    heat 1 and 1.  A size whose shared memory does not fit
- *                    is rejected.
+ *                    the Bridge kernels separately.  Defaults: heat 1 and 1;
+ *                    Euler 2 and 1 while 2 CTAs per block fit one per SM of a
+ *                    B300 (at most 74 blocks), else 1 and 1.  A size whose
+ *                    shared memory does not fit is rejected.
  *   "passes"         row bands each CTA takes one after another per level
  *                    (1, 2, 4): less shared memory per CTA, more CTAs per SM
  *   "profile"        1: every later run brackets each kernel launch with a

@@ -39,6 +39,7 @@ namespace sweep {
 struct HeatAdj {
     static constexpr int NC = 1;
     static constexpr int N = 1;
+    static constexpr int SWEPT_THREADS = 256, STD_THREADS = 256;
 };
 
 template <int C>

@@ -46,10 +46,14 @@ namespace sweep {
 
 namespace cg = cooperative_groups;
 
-#ifndef SWEEP_THREADS
-#define SWEEP_THREADS 256
-#endif
-constexpr int kThreads = SWEEP_THREADS;  // threads per CTA
+// Threads per CTA.  An FP64 warp instruction holds its SM sub-partition's
+// FP64 pipe for 64 cycles, so a few warps per sub-partition suffice; the
+// counts below were measured best per kernel family (Euler 256^2: swept
+// kernels 0.723 / 0.735 / 0.748 / 0.734 Gcell-steps/s at 256 / 384 / 512 /
+// 768 threads, Standard 0.717 / 0.728 / 0.715 / 0.678; heat 4096^2 swept
+// 42.9 / 47.1 / 46.4 at 128 / 256 / 512).  kThreads serves the adjoint's
+// per-cell kernels.
+constexpr int kThreads = 256;
 
 struct Rect {
     int x0, x1, y0, y1;
@@ -100,13 +104,17 @@ struct Params {
 
 // ------------------------------------------------------------------ equations
 
+// NC components, stage radius N, threads per CTA of the swept kernels
+// (SWEPT_THREADS) and of the Standard kernels (STD_THREADS)
 struct Heat {
     static constexpr int NC = 1;
     static constexpr int N = 1;
+    static constexpr int SWEPT_THREADS = 256, STD_THREADS = 256;
 };
 struct Euler {
     static constexpr int NC = 4;
     static constexpr int N = 2;
+    static constexpr int SWEPT_THREADS = 512, STD_THREADS = 384;
 };
 // The same Euler scheme, each computed level also written to the level
 // history of Params (the adjoint's swept recompute); a distinct type so that
@@ -114,12 +122,14 @@ struct Euler {
 struct EulerHist {
     static constexpr int NC = 4;
     static constexpr int N = 2;
+    static constexpr int SWEPT_THREADS = 512, STD_THREADS = 384;
 };
 // Heat with the forward-Euler rule of App. A: every level is a whole step,
 // T^{l} = fma(r, t(T^{l-1}), T^{l-1}); nothing reaches back two levels.
 struct HeatFE {
     static constexpr int NC = 1;
     static constexpr int N = 1;
+    static constexpr int SWEPT_THREADS = 256, STD_THREADS = 256;
 };
 
 // Rows of the largest band a CTA computes: regions lie inside [n, wp-n), so
@@ -723,7 +733,7 @@ __device__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 
 // Up-Pyramid on block (I, J) of the unshifted grid; level 0 is the state.
 template <class EQ, int C>
-__global__ void __launch_bounds__(kThreads) k_up(Params p)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
@@ -747,7 +757,7 @@ __global__ void __launch_bounds__(kThreads) k_up(Params p)
 // X- and Y-Bridges on the seams of the grid with offset o; shape 2t is the
 // X-Bridge right of block t, shape 2t+1 the Y-Bridge above it.
 template <class EQ, int C>
-__global__ void __launch_bounds__(kThreads) k_bridges(Params p, int64_t base, int o)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t base, int o)
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
@@ -771,7 +781,7 @@ __global__ void __launch_bounds__(kThreads) k_bridges(Params p, int64_t base, in
 // last != 0 makes it the Down-Pyramid: the lower half only, after which the
 // window, now complete at level base+d, is written to the state.
 template <class EQ, int C>
-__global__ void __launch_bounds__(kThreads) k_octahedron(Params p, int64_t base, int o, int last)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int64_t base, int o, int last)
 {
     extern __shared__ double smem[];
     Block<EQ, C> B;
@@ -808,7 +818,7 @@ __global__ void __launch_bounds__(kThreads) k_octahedron(Params p, int64_t base,
 // and stage 2 on the tile, and writes the tile to dst (and, if qstar is
 // not null, the tile's first-stage values to qstar).
 template <class EQ>
-__global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *src, double *dst,
+__global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(Params p, const double *src, double *dst,
                                                        double *qstar)
 {
     extern __shared__ double smem[];
@@ -849,7 +859,7 @@ __global__ void __launch_bounds__(kThreads) k_standard(Params p, const double *s
 // One level on every cell (tiles of std_tile with a halo of n): the first
 // RK2 stage (rebuilt for the adjoint), or one forward-Euler step.
 template <class EQ>
-__global__ void __launch_bounds__(kThreads) k_level1(Params p, const double *src, double *dst)
+__global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(Params p, const double *src, double *dst)
 {
     extern __shared__ double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 2 * n;

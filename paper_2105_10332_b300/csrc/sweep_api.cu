@@ -50,7 +50,7 @@ int64_t slot_elems(const sweep_s *h)
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 constexpr size_t kMaxSmem = 227 * 1024;
-constexpr int64_t kStdMinBlocks = 148;  // SMs of a B300
+constexpr int64_t kStdMinBlocks = 148;  // SMs of a B300 (Standard blocks, swept CTAs)
 
 // shared-memory bytes of a swept CTA / a Standard CTA
 size_t swept_smem(int eqn, int b, int C)
@@ -165,7 +165,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
-            k_standard<EQ><<<grid, kThreads, smem, st>>>(p, a, b, nullptr);
+            k_standard<EQ><<<grid, EQ::STD_THREADS, smem, st>>>(p, a, b, nullptr);
         }
         double *t = a;
         a = b;
@@ -174,7 +174,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     if (nlevels & 1) {
         {
             Bracket br(h, st, kKindStandard);
-            k_level1<EQ><<<grid, kThreads, smem1, st>>>(p, a, b);
+            k_level1<EQ><<<grid, EQ::STD_THREADS, smem1, st>>>(p, a, b);
         }
         double *t = a;
         a = b;
@@ -189,18 +189,18 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     return SWEEP_OK;
 }
 
-// launch one swept kernel with C-CTA clusters
+// launch one swept kernel with C-CTA clusters of `threads` threads each
 template <int C, class... KArgs, class... Args>
-cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, size_t smem, cudaStream_t st,
-                   Args... args)
+cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, int threads, size_t smem,
+                   cudaStream_t st, Args... args)
 {
     if constexpr (C == 1) {
-        kernel<<<shapes, kThreads, smem, st>>>(args...);
+        kernel<<<shapes, threads, smem, st>>>(args...);
         return cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(shapes * C, 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -232,19 +232,20 @@ int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
         cudaError_t e;
         {
             Bracket br(h, st, kKindUp);
-            e = launch<C>(k_up<EQ, C>, tiles, smem, st, p);
+            e = launch<C>(k_up<EQ, C>, tiles, EQ::SWEPT_THREADS, smem, st, p);
         }
         for (int64_t c = 0; c <= m && e == cudaSuccess; ++c) {
             const int o = (c & 1) ? h->tile / 2 : 0;
             const int64_t base = c * d;
             {
                 Bracket br(h, st, kKindBridges);
-                e = launch<CB>(k_bridges<EQ, CB>, 2 * tiles, smem_b, st, p, base, o);
+                e = launch<CB>(k_bridges<EQ, CB>, 2 * tiles, EQ::SWEPT_THREADS, smem_b, st, p, base, o);
             }
             if (e != cudaSuccess) break;
             {
                 Bracket br(h, st, c == m ? kKindDown : kKindOctahedron);
-                e = launch<C>(k_octahedron<EQ, C>, tiles, smem, st, p, base, o, c == m ? 1 : 0);
+                e = launch<C>(k_octahedron<EQ, C>, tiles, EQ::SWEPT_THREADS, smem, st, p, base, o,
+                              c == m ? 1 : 0);
             }
         }
         if (e != cudaSuccess) return SWEEP_ECUDA;
@@ -387,7 +388,7 @@ int euler_adjoint(sweep_s *h, const double *q0, const double *lamT, double *lam0
             if (rc != SWEEP_OK) return rc;
         }
         for (int64_t t = swept_levels / 2; t < len; ++t)
-            k_standard<Euler><<<tiles, kThreads, smem_std, st>>>(
+            k_standard<Euler><<<tiles, Euler::STD_THREADS, smem_std, st>>>(
                 p, seg_ptr(t), t + 1 < len ? seg_ptr(t + 1) : mu, qs_ptr(t));
         for (int64_t t = len - 1; t >= 0; --t) {
             k_vjp_cells<<<gc, kThreads, 0, st>>>(p, qs_ptr(t), cp);
@@ -446,9 +447,15 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->limiter = 0;
     h->scheme = 0;
     h->std_tile = 0;
-    // measured on B300 (Euler vortex 256^2, block 32): Octahedra on 2-CTA
-    // clusters, Bridges on single CTAs
-    h->cluster = cluster;
+    // Octahedra of Euler on 2-CTA clusters while the windows' CTAs fit one
+    // per SM (at most 74 windows), else on single CTAs; Bridges on single
+    // CTAs.  Measured on B300 with 512-thread swept CTAs: vortex 256^2
+    // (64 windows) 0.747 Gcell-steps/s with 2-CTA Octahedra; 1024^2 (1024
+    // windows) 0.955 with single CTAs against 0.858 with 2-CTA clusters (a
+    // 512-thread CTA's registers leave room for one CTA per SM).
+    const int64_t windows = (nx / tile) * (ny / tile);
+    h->cluster = (cluster == 2 && 2 * windows > kStdMinBlocks && valid_cluster(eqn, tile, 1))
+                     ? 1 : cluster;
     h->cluster_br = 1;
     h->passes = 1;
     h->profile = 0;

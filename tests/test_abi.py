@@ -141,3 +141,15 @@ def test_standard_tile_default_fills_the_sms(L):
         assert S.sweep_get_param(h, "standard_tile") == expect, (eqn, nx)
         S.sweep_destroy(h)
 
+
+
+def test_euler_octahedron_cluster_default(L):
+    """Euler Octahedra default to 2-CTA clusters while 2 CTAs per block fit one
+    per SM (at most 74 blocks), else to single CTAs; heat to single CTAs."""
+    for eqn, nx, tile, expect in ((S.SWEEP_EULER, 256, 32, 2), (S.SWEEP_EULER, 1024, 32, 1),
+                                  (S.SWEEP_EULER, 64, 32, 2), (S.SWEEP_EULER, 320, 32, 1),
+                                  (S.SWEEP_HEAT, 64, 16, 1)):
+        h = S.sweep_create(eqn, nx, nx, 1e-6, 1.0 / nx, tile, 0)
+        assert S.sweep_get_param(h, "cluster_oct") == expect, (eqn, nx)
+        assert S.sweep_get_param(h, "cluster_bridges") == 1
+        S.sweep_destroy(h)
