@@ -56,7 +56,7 @@ L2_FLUSH_BYTES = 256 << 20
 # rule: its entry is the 4096^2 capture scaled by the 16x windows, since at
 # both sizes the state and the level store are far larger than L2.
 HEAT4096_OCT_TRAFFIC = 652594944 + 248046080
-TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 6117120 + 0,
+TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 6117120 + 1280,
                       ("heat_modes_4096x4096_200steps", "octahedron"): HEAT4096_OCT_TRAFFIC,
                       ("heat_modes_16384x16384_2000steps", "octahedron"): 16 * HEAT4096_OCT_TRAFFIC}
 
