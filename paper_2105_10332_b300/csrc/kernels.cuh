@@ -21,10 +21,13 @@
 // slots, level l in slot l mod (d+1).  A shape writes only the values some
 // other shape reads -- the 2n-wide frame of every Up-Pyramid level, the two
 // 2n-wide bands along a Bridge's seam, and the top level of each shape -- and
-// reads and writes only cells of its own window, and the windows of one
-// launch partition the plane, so no two clusters of a launch touch the same
-// word of a slot.  Within a CTA the full-step levels live in buffer F and the
-// stage levels in buffer H; a second stage updates F in place.
+// reads and writes only cells of its own window.  The windows of an
+// Up-Pyramid or Octahedron launch partition the plane; a block's X- and
+// Y-Bridge windows overlap in one quadrant, where the two shapes read some of
+// the same values but compute and export disjoint regions.  So no word of a
+// slot is written by one cluster and read or written by another within a
+// launch.  Within a CTA the full-step levels live in buffer F and the stage
+// levels in buffer H; a second stage updates F in place.
 //
 // Clusters: with C > 1 every CTA of the cluster keeps a full copy of F and H;
 // CTA r computes the r-th of C row bands of each level, writes the new values
