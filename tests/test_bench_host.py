@@ -1,0 +1,42 @@
+"""bench.py's host-side arithmetic, on CPU: the algorithmic cell-stage counts
+behind the roofline, the CPU oracle sample and the HBM peak lookup."""
+import json
+
+import pytest
+
+
+@pytest.mark.parametrize("eqn,b,d", [("heat", 16, 6), ("heat", 64, 30), ("heat", 32, 2),
+                                     ("euler", 32, 6), ("euler", 24, 4), ("euler", 12, 2)])
+def test_shape_cells_partition_every_cycle(eqn, b, d):
+    """Every (cell, level) is computed once (Sec. 3.3): per cycle the Bridges
+    and the Octahedron together compute each of a block's b^2 cells at d
+    levels, and so do the Up-Pyramid, the first Bridges and the
+    Down-Pyramid of a one-cycle run."""
+    import bench
+    tiles = 7
+    full = tiles * b * b * d
+    cycle = bench.shape_cells(eqn, b, d, "bridges", tiles) + bench.shape_cells(eqn, b, d, "octahedron", tiles)
+    assert cycle == full
+    first = (bench.shape_cells(eqn, b, d, "up_pyramid", tiles) +
+             bench.shape_cells(eqn, b, d, "bridges", tiles) +
+             bench.shape_cells(eqn, b, d, "down_pyramid", tiles))
+    assert first == full
+
+
+def test_oracle_sample_repeats_a_short_workload(oracle_lib):
+    """A workload shorter than the time budget runs again from its initial
+    state, so the sample is bounded by time, not by the workload's length."""
+    import bench
+    from paper_2105_10332_b300 import workloads as W
+    dt, dx = W.heat_dt(16, 0.1)
+    wl = dict(eqn="heat", nx=16, ny=16, dt=dt, dx=dx, nsteps=3, state=W.heat_sine(16, 16))
+    rate, steps, secs = bench.oracle_sample(wl, 0.05)
+    assert steps > wl["nsteps"] and secs >= 0.05 and rate > 0
+
+
+def test_hbm_peak_prefers_the_measured_value(tmp_path, monkeypatch):
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak_gbs() == (bench.HBM_FALLBACK_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6502.2}))
+    assert bench.hbm_peak_gbs() == (6502.2, "measured")
