@@ -226,7 +226,7 @@ def oracle_sample(wl, budget_s):
         if wl["eqn"] == "euler":
             state = oracle.euler_run(state, wl["dt"], wl["dx"], c)
         else:
-            state = oracle.heat_run(state, (wl["dt"]) / (wl["dx"] * wl["dx"]), c)
+            state = oracle.heat_run(state, c, wl["dt"], wl["dx"])
         t_total += time.perf_counter() - t0
         steps += c
         in_run += c

@@ -6,13 +6,15 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 no code with the CUDA library.
 
 Functions (each follows the passage cited in the C source):
+  heat_r         -- App. A mesh ratio r = alpha dt / dx^2 from the physical inputs
   heat_run       -- App. A heat update, RK2 midpoint (scheme 0) or forward Euler (1)
   euler_run      -- App. B Euler scheme: pressure minmod, Rusanov-form flux, RK2
   swept_replay   -- the Sec. 3.3 phase schedule replayed cell by cell with
                     dependency checks (Eq. 1 bounds the depth)
   heat_adjoint, euler_adjoint -- discrete adjoints (reverse mode) of the two
                     schemes, with checkpointing for Euler
-  face_flux, limiter, state_flux -- single-face pieces used by the pins
+  face_flux, limiter, state_flux, cell_pressure -- single-face and single-cell
+                    pieces used by the pins
 """
 import ctypes
 
@@ -33,7 +35,10 @@ def lib():
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         i64 = ctypes.c_int64
-        L.oracle_heat_run.argtypes = [i64, i64, ctypes.c_double, ctypes.c_int, dp, i64]
+        dbl = ctypes.c_double
+        L.oracle_heat_r.argtypes = [dbl, dbl, dbl]
+        L.oracle_heat_r.restype = dbl
+        L.oracle_heat_run.argtypes = [i64, i64, dbl, dbl, dbl, ctypes.c_int, dp, i64]
         L.oracle_heat_run.restype = ctypes.c_int
         L.oracle_euler_run.argtypes = [i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, dp, i64]
@@ -49,11 +54,13 @@ def lib():
                                           ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.c_int]
         L.oracle_swept_replay.restype = ctypes.c_int
-        L.oracle_heat_adjoint.argtypes = [i64, i64, ctypes.c_double, dp, i64]
+        L.oracle_heat_adjoint.argtypes = [i64, i64, dbl, dbl, dbl, dp, i64]
         L.oracle_heat_adjoint.restype = ctypes.c_int
         L.oracle_euler_adjoint.argtypes = [i64, i64, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, dp, dp, i64, i64]
         L.oracle_euler_adjoint.restype = ctypes.c_int
+        L.oracle_cell_pressure.argtypes = [dp, dbl]
+        L.oracle_cell_pressure.restype = dbl
         _lib = L
     return _lib
 
@@ -68,11 +75,19 @@ def _check(rc, what):
         raise RuntimeError("oracle %s failed: %s (%d)" % (what, ERRORS.get(rc, "?"), rc))
 
 
-def heat_run(u0, r, nsteps, scheme=0):
-    """Advance the periodic heat field u0 [ny, nx] by nsteps (App. A); returns a new array."""
+def heat_r(dt, dx, alpha=1.0):
+    """App. A mesh ratio r = alpha dt / dx^2, as the oracle evaluates it."""
+    return float(lib().oracle_heat_r(float(alpha), float(dt), float(dx)))
+
+
+def heat_run(u0, nsteps, dt, dx, alpha=1.0, scheme=0):
+    """Advance the periodic heat field u0 [ny, nx] by nsteps time steps of size dt
+    on a grid of spacing dx (dy = dx) with diffusivity alpha (App. A); returns a
+    new array.  The oracle forms r = alpha dt / dx^2 itself."""
     u = np.ascontiguousarray(u0, dtype=np.float64).copy()
     ny, nx = u.shape
-    _check(lib().oracle_heat_run(nx, ny, float(r), int(scheme), _dptr(u), int(nsteps)), "heat_run")
+    _check(lib().oracle_heat_run(nx, ny, float(alpha), float(dt), float(dx), int(scheme), _dptr(u),
+                                 int(nsteps)), "heat_run")
     return u
 
 
@@ -108,11 +123,13 @@ def swept_replay(eqn, state0, tile, depth, nsteps, c1, c2, gamma=1.4, limiter=0,
     return s, stats
 
 
-def heat_adjoint(lamT, r, nsteps):
-    """(A^T)^N lamT for the RK2 heat step A (App. A): the gradient of <u_N, lamT> w.r.t. u_0."""
+def heat_adjoint(lamT, nsteps, dt, dx, alpha=1.0):
+    """(A^T)^N lamT for the RK2 heat step A (App. A) with r = alpha dt / dx^2:
+    the gradient of <u_N, lamT> with respect to u_0."""
     lam = np.ascontiguousarray(lamT, dtype=np.float64).copy()
     ny, nx = lam.shape
-    _check(lib().oracle_heat_adjoint(nx, ny, float(r), _dptr(lam), int(nsteps)), "heat_adjoint")
+    _check(lib().oracle_heat_adjoint(nx, ny, float(alpha), float(dt), float(dx), _dptr(lam),
+                                     int(nsteps)), "heat_adjoint")
     return lam
 
 
@@ -141,6 +158,12 @@ def limiter(dm, dp, kind=0):
     b = np.zeros(1)
     lib().oracle_limiter(float(dm), float(dp), int(kind), _dptr(a), _dptr(b))
     return float(a[0]), float(b[0])
+
+
+def cell_pressure(q, gamma=1.4):
+    """Pressure of one conserved state (rho, rho u, rho v, E) as the limiter forms it."""
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    return float(lib().oracle_cell_pressure(_dptr(qa), float(gamma)))
 
 
 def state_flux(q, gamma=1.4):

@@ -83,11 +83,22 @@ static void heat_stage(int64_t nx, int64_t ny, double c, const double *src,
             out[j * nx + i] = fma(c, heat_t(src, nx, ny, i, j), own[j * nx + i]);
 }
 
-/* scheme 0: RK2 midpoint; scheme 1: forward Euler (App. A update) */
-int oracle_heat_run(int64_t nx, int64_t ny, double r, int scheme, double *u, int64_t nsteps)
+/* The mesh ratio of App. A, r = alpha dt / dx^2 (dy = dx, so r_x = r_y = r),
+ * evaluated as written: the product alpha dt over the square dx dx. */
+double oracle_heat_r(double alpha, double dt, double dx)
 {
-    if (nx < 3 || ny < 3 || nsteps < 0 || (scheme != 0 && scheme != 1))
+    return (alpha * dt) / (dx * dx);
+}
+
+/* scheme 0: RK2 midpoint; scheme 1: forward Euler (App. A update).  The
+ * coefficient r comes from the physical inputs (alpha, dt, dx) of App. A. */
+int oracle_heat_run(int64_t nx, int64_t ny, double alpha, double dt, double dx, int scheme,
+                    double *u, int64_t nsteps)
+{
+    if (nx < 3 || ny < 3 || nsteps < 0 || (scheme != 0 && scheme != 1) || !(dx > 0.0) ||
+        !(alpha > 0.0) || !(dt > 0.0))
         return ORACLE_EINVAL;
+    const double r = oracle_heat_r(alpha, dt, dx);
     double *a = (double *)malloc(sizeof(double) * (size_t)(nx * ny));
     double *b = (double *)malloc(sizeof(double) * (size_t)(nx * ny));
     if (!a || !b) {
@@ -345,6 +356,12 @@ void oracle_face_flux(const double *qm1, const double *q0, const double *q1, con
     const double p1 = cell_pressure(q1[0], q1[1], q1[2], q1[3], gamma);
     const double p2 = cell_pressure(q2[0], q2[1], q2[2], q2[3], gamma);
     face_flux(qm1, q0, q1, q2, pm1, p0, p1, p2, gamma, limiter, fh);
+}
+
+/* cell pressure of one conserved state (rho, m_x, m_y, E), exposed for its pin */
+double oracle_cell_pressure(const double *q, double gamma)
+{
+    return cell_pressure(q[0], q[1], q[2], q[3], gamma);
 }
 
 /* limiter factors of one cell, exposed for the minmod pin */
@@ -678,10 +695,12 @@ int oracle_swept_replay(int eqn, int64_t nx, int64_t ny, int64_t b, int d, int64
 /* Heat: the step Q' = Q + c2 L(Q + c1 L Q) with symmetric L.  Adjoint step
  * (order pinned): mu* = c2 * t(lam); lam_n = fma(c1, t(mu*), lam + mu*),
  * t(u) = fma(-4, u, (u_W + u_E) + (u_S + u_N)). */
-int oracle_heat_adjoint(int64_t nx, int64_t ny, double r, double *lam, int64_t nsteps)
+int oracle_heat_adjoint(int64_t nx, int64_t ny, double alpha, double dt, double dx, double *lam,
+                        int64_t nsteps)
 {
-    if (nx < 3 || ny < 3 || nsteps < 0)
+    if (nx < 3 || ny < 3 || nsteps < 0 || !(dx > 0.0) || !(alpha > 0.0) || !(dt > 0.0))
         return ORACLE_EINVAL;
+    const double r = oracle_heat_r(alpha, dt, dx);
     const size_t n = (size_t)(nx * ny);
     double *ms = (double *)malloc(sizeof(double) * n);
     double *out = (double *)malloc(sizeof(double) * n);
@@ -810,14 +829,12 @@ static void limiter_grad(int limiter, int plus, double dm, double dp, double *d_
 
 /* Reverse of face_flux at the face between cells 0 and 1 of the line
  * (-1, 0, 1, 2), states in the face-normal frame.  a[4]: adjoint of the
- * numerical flux.  Accumulates into qbar[1] and qbar[2] (cells 0 and 1) the
- * gradient through the reconstructed states, and returns in pbar[m] the
- * adjoint of the cell pressure P(q[m]) of each of the four cells (the
- * limiter's inputs).  The pressure's own reverse (cell_pressure_bar) is
- * linear in pbar and the same for every face of a cell, so the callers
- * apply it once per cell to the summed pbar. */
+ * numerical flux.  Accumulates into qbar[m][4], m = 0..3 (cells -1..2), the
+ * whole gradient of <a, Fh>: through the reconstructed states into cells 0
+ * and 1, and through the limiter's pressures into all four cells, each
+ * pressure reversed right here for this face (chain rule, face by face). */
 static void face_flux_bar(const double *q[4], double gamma, int limiter, const double a[4],
-                          double qbar[4][4], double pbar[4])
+                          double qbar[4][4])
 {
     double p[4];
     for (int m = 0; m < 4; ++m)
@@ -863,9 +880,7 @@ static void face_flux_bar(const double *q[4], double gamma, int limiter, const d
         qbar[2][k] += qrbar[k] + dqbar;
     }
     /* hl = phi0p / 2 from (p0 - pm1, p1 - p0); hr = phi1m / 2 from (p1 - p0, p2 - p1) */
-    double g_dm, g_dp;
-    for (int m = 0; m < 4; ++m)
-        pbar[m] = 0.0;
+    double pbar[4] = {0, 0, 0, 0}, g_dm, g_dp;
     limiter_grad(limiter, 1, p[1] - p[0], p[2] - p[1], &g_dm, &g_dp);
     pbar[1] += 0.5 * hlbar * g_dm;
     pbar[0] -= 0.5 * hlbar * g_dm;
@@ -876,21 +891,19 @@ static void face_flux_bar(const double *q[4], double gamma, int limiter, const d
     pbar[1] -= 0.5 * hrbar * g_dm;
     pbar[3] += 0.5 * hrbar * g_dp;
     pbar[2] -= 0.5 * hrbar * g_dp;
+    for (int m = 0; m < 4; ++m)
+        cell_pressure_bar(q[m], gamma, pbar[m], qbar[m]);
 }
 
 /* out = J^T v for the residual d(Q)_c = (Fh_{i-1/2} - Fh_{i+1/2}) + (Gh_{j-1/2}
  * - Gh_{j+1/2}) of every cell (out is overwritten).  Each face, visited x
- * faces then y faces in raster order, adds its contribution for
- * a = v_{right} - v_{left} through face_flux_bar: the gradient through its
- * reconstructed states to its two cells' out, and the adjoints of its four
- * cells' pressures to pb (plane doubles, scratch).  Then every cell adds
- * the reverse of its pressure for the summed pb. */
-static void euler_residual_vjp(const double *q, const double *v, double *out, double *pb,
-                               int64_t nx, int64_t ny, double gamma, int limiter)
+ * faces then y faces in raster order, adds its whole contribution for
+ * a = v_{right} - v_{left} (face_flux_bar) to the four cells of its line. */
+static void euler_residual_vjp(const double *q, const double *v, double *out, int64_t nx,
+                               int64_t ny, double gamma, int limiter)
 {
     const int64_t plane = nx * ny;
     memset(out, 0, sizeof(double) * (size_t)(4 * plane));
-    memset(pb, 0, sizeof(double) * (size_t)plane);
     for (int axis = 0; axis < 2; ++axis)
         for (int64_t j = 0; j < ny; ++j)
             for (int64_t i = 0; i < nx; ++i) {
@@ -912,23 +925,14 @@ static void euler_residual_vjp(const double *q, const double *v, double *out, do
                     const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
                     a[k] = v[kk * plane + cr] - v[kk * plane + cl];
                 }
-                double qb[4][4] = {{0}}, pbar[4];
-                face_flux_bar(qp, gamma, limiter, a, qb, pbar);
-                for (int m = 1; m <= 2; ++m)
+                double qb[4][4] = {{0}};
+                face_flux_bar(qp, gamma, limiter, a, qb);
+                for (int m = 0; m < 4; ++m)
                     for (int k = 0; k < 4; ++k) {
                         const int kk = (axis == 1 && (k == 1 || k == 2)) ? 3 - k : k;
                         out[kk * plane + idx[m]] += qb[m][k];
                     }
-                for (int m = 0; m < 4; ++m)
-                    pb[idx[m]] += pbar[m];
             }
-    for (int64_t c = 0; c < plane; ++c) {
-        const double qc[4] = {q[c], q[plane + c], q[2 * plane + c], q[3 * plane + c]};
-        double ob[4] = {out[c], out[plane + c], out[2 * plane + c], out[3 * plane + c]};
-        cell_pressure_bar(qc, gamma, pb[c], ob);
-        for (int k = 0; k < 4; ++k)
-            out[k * plane + c] = ob[k];
-    }
 }
 
 /* One adjoint RK2 step at Q^n (RK2: Q* = Q + lam1 d(Q), Q' = Q + lam2 d(Q*)):
@@ -936,14 +940,14 @@ static void euler_residual_vjp(const double *q, const double *v, double *out, do
  *   lam  = lam' + mu* + lam1 J(Q)^T mu*                                  */
 static void euler_adjoint_step(const double *q, double *lam, int64_t nx, int64_t ny, double lam1,
                                double lam2, double gamma, int limiter, double *qs, double *ms,
-                               double *tmp, double *pb)
+                               double *tmp)
 {
     const int64_t n4 = 4 * nx * ny;
     euler_stage(nx, ny, lam1, gamma, limiter, q, q, qs); /* Q* */
-    euler_residual_vjp(qs, lam, tmp, pb, nx, ny, gamma, limiter);
+    euler_residual_vjp(qs, lam, tmp, nx, ny, gamma, limiter);
     for (int64_t k = 0; k < n4; ++k)
         ms[k] = lam2 * tmp[k];
-    euler_residual_vjp(q, ms, tmp, pb, nx, ny, gamma, limiter);
+    euler_residual_vjp(q, ms, tmp, nx, ny, gamma, limiter);
     for (int64_t k = 0; k < n4; ++k)
         lam[k] = lam[k] + ms[k] + lam1 * tmp[k];
 }
@@ -963,14 +967,12 @@ int oracle_euler_adjoint(int64_t nx, int64_t ny, double dt, double dx, double ga
     double *qs = (double *)malloc(sizeof(double) * n4);
     double *ms = (double *)malloc(sizeof(double) * n4);
     double *tmp = (double *)malloc(sizeof(double) * n4);
-    double *pb = (double *)malloc(sizeof(double) * (size_t)(nx * ny));
-    if (!cps || !seg || !qs || !ms || !tmp || !pb) {
+    if (!cps || !seg || !qs || !ms || !tmp) {
         free(cps);
         free(seg);
         free(qs);
         free(ms);
         free(tmp);
-        free(pb);
         return ORACLE_ENOMEM;
     }
     const double lam2 = dt / dx, lam1 = 0.5 * lam2;
@@ -996,14 +998,13 @@ int oracle_euler_adjoint(int64_t nx, int64_t ny, double dt, double dx, double ga
         }
         for (int64_t t = len - 1; t >= 0; --t)
             euler_adjoint_step(seg + (size_t)t * n4, lam, nx, ny, lam1, lam2, gamma, limiter, qs,
-                               ms, tmp, pb);
+                               ms, tmp);
     }
     free(cps);
     free(seg);
     free(qs);
     free(ms);
     free(tmp);
-    free(pb);
     return ORACLE_OK;
 }
 
@@ -1013,10 +1014,8 @@ void oracle_face_flux_vjp(const double *qm1, const double *q0, const double *q1,
                           double gamma, int limiter, const double *a, double *qbar)
 {
     const double *q[4] = {qm1, q0, q1, q2};
-    double qb[4][4] = {{0}}, pbar[4];
-    face_flux_bar(q, gamma, limiter, a, qb, pbar);
-    for (int m = 0; m < 4; ++m)
-        cell_pressure_bar(q[m], gamma, pbar[m], qb[m]);
+    double qb[4][4] = {{0}};
+    face_flux_bar(q, gamma, limiter, a, qb);
     for (int m = 0; m < 4; ++m)
         for (int k = 0; k < 4; ++k)
             qbar[4 * m + k] += qb[m][k];

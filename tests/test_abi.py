@@ -108,6 +108,20 @@ def test_adjoint_workspace_and_argument_checks(L):
     S.sweep_destroy(hh)
 
 
+def test_heat_coefficient_matches_the_oracle(L, oracle_lib):
+    """The library's heat coefficient r = alpha dt / dx^2 (App. A) is the
+    oracle's, bit for bit, for the workloads' sides (powers of two and not)
+    and diffusivities other than 1: both evaluate the formula as written."""
+    from paper_2105_10332_b300 import workloads as W
+    for n, tile in ((64, 16), (48, 12), (72, 12), (80, 20), (96, 16), (4096, 64), (16384, 64)):
+        for alpha, r in ((1.0, 0.1), (0.7, 0.2), (2.5, 0.05)):
+            dt, dx = W.heat_dt(n, r, alpha)
+            h = S.sweep_create(S.SWEEP_HEAT, n, n, dt, dx, tile, 0)
+            S.sweep_set_param(h, "alpha", alpha)
+            assert S.sweep_get_param(h, "r") == oracle_lib.heat_r(dt, dx, alpha), (n, alpha)
+            S.sweep_destroy(h)
+
+
 def test_autotune_candidates_are_legal():
     from paper_2105_10332_b300 import autotune
     for eqn in ("heat", "euler"):

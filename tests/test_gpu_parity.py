@@ -16,6 +16,7 @@ from paper_2105_10332_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 REL = 1e-12
+EPS = np.finfo(np.float64).eps
 
 
 @pytest.fixture(scope="module")
@@ -45,10 +46,13 @@ def gpu_run(torch, solver, state_np, nsteps, method, poison=True):
 
 
 def heat_solver(S, nx, ny, tile, depth, r=0.1, **kw):
+    """A heat solver at mesh ratio r (App. A: r = alpha dt / dx^2, alpha = 1,
+    dx = 1/nx).  Returns (solver, dt, dx): the oracle gets the same physical
+    inputs and forms r itself, so nothing the library computes feeds it."""
     dt, dx = W.heat_dt(nx, r)
-    # r is recomputed inside as alpha dt / dx^2; check it reproduces the oracle's r
     s = S.Solver("heat", nx, ny, dt, dx, tile, depth, **kw)
-    return s, s.get("r")
+    assert abs(s.get("r") - r) <= 4 * EPS * r
+    return s, dt, dx
 
 
 def euler_solver(S, nx, ny, tile, depth, T=1.0, **kw):
@@ -61,9 +65,9 @@ def euler_solver(S, nx, ny, tile, depth, T=1.0, **kw):
 
 def test_heat_standard_matches_oracle_sine64(torch_cuda, oracle_lib):
     from paper_2105_10332_b300 import sweep as S
-    s, r = heat_solver(S, 64, 64, 16, 6)
+    s, dt, dx = heat_solver(S, 64, 64, 16, 6)
     u0 = W.heat_sine(64, 64)
-    ref = oracle_lib.heat_run(u0, r, 500)
+    ref = oracle_lib.heat_run(u0, 500, dt, dx)
     got = gpu_run(torch_cuda, s, u0, 500, "run_standard")
     e = relerr(got, ref)
     assert e <= REL, e
@@ -79,9 +83,9 @@ def test_heat_swept_bit_identical(torch_cuda, oracle_lib, nx, ny, tile, nsteps):
     k = tile // 2 - 1
     ref = None
     for d in range(2, k + 1, 2):
-        s, r = heat_solver(S, nx, ny, tile, d)
+        s, dt, dx = heat_solver(S, nx, ny, tile, d)
         if ref is None:
-            ref = oracle_lib.heat_run(u0, r, nsteps)
+            ref = oracle_lib.heat_run(u0, nsteps, dt, dx)
             std = gpu_run(torch_cuda, s, u0, nsteps, "run_standard")
             assert np.array_equal(std, ref), relerr(std, ref)
         sw = gpu_run(torch_cuda, s, u0, nsteps, "run_swept")
@@ -92,12 +96,12 @@ def test_heat_swept_sine64_and_closed_form(torch_cuda, oracle_lib):
     """Heat sine 64^2, r = 0.1, 500 steps, tile 16: Swept = Standard = oracle,
     and the discrete closed form G^500 within 1e-13."""
     from paper_2105_10332_b300 import sweep as S
-    s, r = heat_solver(S, 64, 64, 16, 6)
+    s, dt, dx = heat_solver(S, 64, 64, 16, 6)
     u0 = W.heat_sine(64, 64)
     sw = gpu_run(torch_cuda, s, u0, 500, "run_swept")
-    ref = oracle_lib.heat_run(u0, r, 500)
+    ref = oracle_lib.heat_run(u0, 500, dt, dx)
     assert np.array_equal(sw, ref), relerr(sw, ref)
-    z = r * (-8.0 * math.sin(math.pi / 64) ** 2)
+    z = 0.1 * (-8.0 * math.sin(math.pi / 64) ** 2)  # the workload's r = 0.1
     G = 1 + z + 0.5 * z * z
     assert relerr(sw, G ** 500 * u0) <= 1e-13
 
@@ -146,14 +150,14 @@ def test_constant_states_preserved(torch_cuda):
     q = np.stack([np.full((64, 64), x) for x in (rho, rho * u, rho * v,
                                                 p / 0.4 + 0.5 * rho * (u * u + v * v))])
     assert np.array_equal(gpu_run(torch_cuda, s, q, 13, "run_swept"), q)
-    h, _ = heat_solver(S, 64, 64, 16, 6)
+    h, _, _ = heat_solver(S, 64, 64, 16, 6)
     c = np.full((64, 64), -3.25)
     assert np.array_equal(gpu_run(torch_cuda, h, c, 13, "run_swept"), c)
 
 
 def test_zero_steps_is_identity(torch_cuda):
     from paper_2105_10332_b300 import sweep as S
-    h, _ = heat_solver(S, 64, 64, 16, 6)
+    h, _, _ = heat_solver(S, 64, 64, 16, 6)
     u0 = W.heat_modes(64, 64, seed=2)
     assert np.array_equal(gpu_run(torch_cuda, h, u0, 0, "run_swept"), u0)
 
@@ -200,7 +204,7 @@ def test_heat_large_sampled_closed_form(torch_cuda):
     n, N = 4096, 200
     dt, dx = W.heat_dt(n, 0.1)
     s = S.Solver("heat", n, n, dt, dx, 32, 14)
-    r = s.get("r")
+    r = 0.1  # the workload's mesh ratio, not the library's
     u0 = W.heat_modes(n, n)
     a = torch.from_numpy(u0).cuda()
     b = a.clone()
@@ -238,7 +242,7 @@ def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, passes, eq
         if eqn == "euler":
             s, q0, dt, dx = euler_solver(S, nx, ny, tile, d)
         else:
-            s, _ = heat_solver(S, nx, ny, tile, d)
+            s, hdt, hdx = heat_solver(S, nx, ny, tile, d)
             q0 = W.heat_modes(nx, ny, seed=tile + d)
         try:
             s.set("cluster", cluster)
@@ -249,7 +253,7 @@ def test_cluster_sizes_bit_identical(torch_cuda, oracle_lib, cluster, passes, eq
             if eqn == "euler":
                 ref = oracle_lib.euler_run(q0, dt, dx, N)
             else:
-                ref = oracle_lib.heat_run(q0, s.get("r"), N)
+                ref = oracle_lib.heat_run(q0, N, hdt, hdx)
             got = gpu_run(torch_cuda, s, q0, N, "run_swept")
             assert np.array_equal(got, ref), (cluster, d, N, relerr(got, ref))
 
@@ -264,7 +268,7 @@ def test_heat_modes16384_full_size(torch_cuda):
     n, N = 16384, 2000
     dt, dx = W.heat_dt(n, 0.1)
     s = S.Solver("heat", n, n, dt, dx, 64, 30)
-    r = s.get("r")
+    r = 0.1  # the workload's mesh ratio, not the library's
     u0 = W.heat_modes(n, n)
     a = torch.from_numpy(u0).cuda()
     b = a.clone()

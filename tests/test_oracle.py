@@ -26,10 +26,35 @@ def heat_growth(kx, ky, nx, ny, r, scheme):
     return 1.0 + z + 0.5 * z * z if scheme == 0 else 1.0 + z
 
 
+def heat_run_r(oracle_lib, u0, r, nsteps, scheme=0):
+    """Heat run at mesh ratio r: dx = 1/nx and dt = r dx^2 (alpha = 1) handed to
+    the oracle, which forms r = alpha dt / dx^2 itself."""
+    dt, dx = W.heat_dt(u0.shape[-1], r)
+    return oracle_lib.heat_run(u0, nsteps, dt, dx, scheme=scheme)
+
+
+def test_heat_r_is_alpha_dt_over_dx_squared(oracle_lib):
+    """App. A: r = alpha dt / dx^2.  The oracle's value against exact rational
+    arithmetic (a dropped alpha, dx in place of dx^2 or an inverted ratio fails)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    for _ in range(500):
+        alpha = float(rng.uniform(0.1, 3.0))
+        dx = 1.0 / int(rng.integers(8, 20000))
+        dt = float(rng.uniform(0.01, 0.3)) * dx * dx / alpha
+        exact = Fraction(alpha) * Fraction(dt) / (Fraction(dx) * Fraction(dx))
+        got = oracle_lib.heat_r(dt, dx, alpha)
+        assert abs(Fraction(got) - exact) <= 2 * EPS * exact
+    # powers of two make every step exact: r = 0.1 at 64^2 comes back as the double 0.1
+    dt, dx = W.heat_dt(64, 0.1)
+    assert oracle_lib.heat_r(dt, dx) == 0.1 and dt == 0.1 / 4096
+    assert oracle_lib.heat_r(dt, dx, 2.0) == 0.2
+
+
 def test_heat_closed_form_sine_64(oracle_lib):
     """Heat 64^2, r = 0.1, 500 RK2 steps of T0 = sin 2pi x sin 2pi y (App. A)."""
     u0 = W.heat_sine(64, 64)
-    u = oracle_lib.heat_run(u0, 0.1, 500)
+    u = heat_run_r(oracle_lib, u0, 0.1, 500)
     G = heat_growth(1, 1, 64, 64, 0.1, 0)
     assert abs(G ** 500 - 0.38172528846400894) < 1e-15
     err = np.max(np.abs(u - G ** 500 * u0)) / np.max(np.abs(u0))
@@ -47,7 +72,7 @@ def test_heat_closed_form_modes(oracle_lib, scheme):
         mode = np.outer(np.sin(2 * math.pi * ky * y + phy), np.sin(2 * math.pi * kx * x + phx))
         u0 += a * mode
         expect += a * heat_growth(kx, ky, nx, ny, r, scheme) ** N * mode
-    u = oracle_lib.heat_run(u0, r, N, scheme=scheme)
+    u = heat_run_r(oracle_lib, u0, r, N, scheme=scheme)
     err = np.max(np.abs(u - expect)) / np.max(np.abs(u0))
     assert err <= 1e-13, err
 
@@ -57,11 +82,11 @@ def test_heat_vs_analytic(oracle_lib):
     decayed amplitude, is the O(dx^2) truncation error of the 5-point Laplacian,
     predicted (pi/64)^2/3 * 8 pi^2 t = 7.75e-4."""
     nx, r, N = 64, 0.1, 500
-    dt, _ = W.heat_dt(nx, r)
+    dt, dx = W.heat_dt(nx, r)
     t = N * dt
     assert t == 0.01220703125
     u0 = W.heat_sine(nx, nx)
-    u = oracle_lib.heat_run(u0, r, N)
+    u = oracle_lib.heat_run(u0, N, dt, dx)
     decay = math.exp(-8 * math.pi ** 2 * t)
     gap = np.max(np.abs(u - decay * u0)) / (decay * np.max(np.abs(u0)))
     predicted = (math.pi / nx) ** 2 / 3 * 8 * math.pi ** 2 * t
@@ -72,7 +97,7 @@ def test_heat_vs_analytic(oracle_lib):
 def test_heat_conservation(oracle_lib):
     u0 = W.heat_modes(40, 36, seed=3) + 0.25
     N = 300
-    u = oracle_lib.heat_run(u0, 0.1, N)
+    u = heat_run_r(oracle_lib, u0, 0.1, N)
     drift = abs(math.fsum(u.ravel()) - math.fsum(u0.ravel()))
     assert drift <= 64 * EPS * N * math.fsum(np.abs(u0).ravel())
 
@@ -80,11 +105,12 @@ def test_heat_conservation(oracle_lib):
 def test_heat_transpose_and_constant(oracle_lib):
     rng = np.random.default_rng(11)
     u0 = rng.standard_normal((24, 36))
-    a = oracle_lib.heat_run(u0, 0.1, 17)
-    b = oracle_lib.heat_run(np.ascontiguousarray(u0.T), 0.1, 17)
+    dt, dx = W.heat_dt(36, 0.1)
+    a = oracle_lib.heat_run(u0, 17, dt, dx)
+    b = oracle_lib.heat_run(np.ascontiguousarray(u0.T), 17, dt, dx)
     assert np.array_equal(a.T, b)
     c = np.full((20, 20), 0.7135)
-    assert np.array_equal(oracle_lib.heat_run(c, 0.1, 25), c)
+    assert np.array_equal(heat_run_r(oracle_lib, c, 0.1, 25), c)
 
 
 def test_heat_brute_force_single_point(oracle_lib):
@@ -92,7 +118,7 @@ def test_heat_brute_force_single_point(oracle_lib):
     Euler step the centre holds 1 - 4r and each neighbour r (exact in binary for r = 1/8)."""
     u0 = np.zeros((8, 8))
     u0[3, 4] = 1.0
-    u = oracle_lib.heat_run(u0, 0.125, 1, scheme=1)
+    u = heat_run_r(oracle_lib, u0, 0.125, 1, scheme=1)
     expect = np.zeros((8, 8))
     expect[3, 4] = 0.5
     for j, i in ((2, 4), (4, 4), (3, 3), (3, 5)):
@@ -100,7 +126,7 @@ def test_heat_brute_force_single_point(oracle_lib):
     assert np.array_equal(u, expect)
     # RK2 midpoint: one step is u + r L u + (r^2/2) L^2 u; L^2 of a delta has
     # centre 20, ring-1 -8, diagonals 2, ring-2 1.
-    u = oracle_lib.heat_run(u0, 0.125, 1, scheme=0)
+    u = heat_run_r(oracle_lib, u0, 0.125, 1, scheme=0)
     r = 0.125
     L2 = np.zeros((8, 8))
     L2[3, 4] = 20
@@ -156,6 +182,64 @@ def test_rusanov_sod_states(oracle_lib):
     expect = np.array([0.5 * s * 0.875, 0.5 * 1.1, 0.0, 0.5 * s * 2.25])
     assert fh[2] == 0.0
     assert np.max(np.abs(fh - expect)) <= 16 * EPS
+
+
+def test_cell_pressure_from_primitives(oracle_lib):
+    """The limiter's pressure is the App. B EOS p = (gamma-1)(E - rho(u^2+v^2)/2)
+    of the conserved state: states built from primitives give their p back.
+    A wrong kinetic term (E - rho|u|^2, or E alone) or a wrong factor fails."""
+    q = np.array([2.0, 3.0, -1.0, 10.0])  # rho 2, u 1.5, v -0.5: E - KE = 7.5 exactly
+    assert abs(oracle_lib.cell_pressure(q) - 0.4 * 7.5) <= 4 * EPS * 3.0
+    rng = np.random.default_rng(23)
+    for _ in range(200):
+        rho, p = rng.uniform(0.3, 3.0, 2)
+        u, v = rng.uniform(-1.5, 1.5, 2)
+        q = conserved(rho, u, v, p)
+        assert abs(oracle_lib.cell_pressure(q) - p) <= 64 * EPS * (p + 0.5 * rho * (u * u + v * v))
+    # symmetric in x and y
+    q = conserved(1.3, 0.9, -0.2, 1.7)
+    assert oracle_lib.cell_pressure(q) == oracle_lib.cell_pressure(q[[0, 2, 1, 3]])
+
+
+def rusanov_by_hand(qa, qb, gamma=GAMMA):
+    """1/2 (F(QL) + F(QR) + max(|u_n|+c) (QL - QR)) from primitives, in numpy."""
+    out = []
+    for q in (qa, qb):
+        rho, mn, mt, E = q
+        un, ut = mn / rho, mt / rho
+        p = (gamma - 1.0) * (E - 0.5 * rho * (un * un + ut * ut))
+        c = math.sqrt(gamma * p / rho)
+        out.append((np.array([mn, mn * un + p, mt * un, (E + p) * un]), abs(un) + c))
+    (fa, la), (fb, lb) = out
+    return 0.5 * (fa + fb + max(la, lb) * (qa - qb))
+
+
+def test_face_flux_limiter_sees_cell_pressures(oracle_lib):
+    """Four cells of a line with pressures 1, 2, 4, 5 and different velocities:
+    theta = dm/dp = 1/2 on cell 0 towards its + face and dp/dm = 1/2 on cell 1
+    towards its - face, so Q_L = Q_0 + (Q_1 - Q_0)/4 and Q_R = Q_1 - (Q_1 - Q_0)/4
+    (App. B reconstruction with phi/2 = 1/4), and the face flux is the Rusanov
+    flux of those two states.  The limiter takes its pressures from the
+    conserved states, so a wrong kinetic-energy term moves theta and fails here."""
+    prims = [(1.0, 0.5, 0.25, 1.0), (1.25, 0.75, -0.5, 2.0), (0.8, 1.0, 0.5, 4.0),
+             (1.1, 0.25, 0.0, 5.0)]
+    qs = [conserved(*pr) for pr in prims]
+    for lim in (0, 1):
+        # the printed orientation (1) takes dp/dm on cell 0 and dm/dp on cell 1: both 2 -> 1
+        h = 0.25 if lim == 0 else 0.5
+        ql = qs[1] + h * (qs[2] - qs[1])
+        qr = qs[2] - h * (qs[2] - qs[1])
+        got = oracle_lib.face_flux(*qs, limiter=lim)
+        exp = rusanov_by_hand(ql, qr)
+        assert np.max(np.abs(got - exp)) <= 1e-13 * np.max(np.abs(exp)), (lim, got, exp)
+    # the same line with the kinetic term doubled in the limiter's pressure would
+    # give theta = 0.429 on cell 0; the resulting flux differs at the 1e-3 level
+    k = [0.5 * r * (u * u + v * v) for r, u, v, _ in prims]
+    pw = [p - 0.4 * kk for (_, _, _, p), kk in zip(prims, k)]
+    th = (pw[1] - pw[0]) / (pw[2] - pw[1])
+    wrong = rusanov_by_hand(qs[1] + 0.5 * th * (qs[2] - qs[1]),
+                            qs[2] - 0.5 * min((pw[3] - pw[2]) / (pw[2] - pw[1]), 1.0) * (qs[2] - qs[1]))
+    assert np.max(np.abs(wrong - oracle_lib.face_flux(*qs))) > 1e-4
 
 
 def minmod(a, b):
@@ -273,8 +357,9 @@ def heat_cases():
 @pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 7, 13])
 def test_replay_heat_equals_step_by_step(oracle_lib, nx, ny, b, d, nsteps):
     u0 = W.heat_modes(nx, ny, seed=nx + b + d)
-    r = 0.1
-    ref = oracle_lib.heat_run(u0, r, nsteps)
+    dt, dx = W.heat_dt(nx, 0.1)
+    r = oracle_lib.heat_r(dt, dx)
+    ref = oracle_lib.heat_run(u0, nsteps, dt, dx)
     out, st = oracle_lib.swept_replay(0, u0, b, d, nsteps, 0.5 * r, r)
     assert np.array_equal(out, ref)
     assert st["cells"] == 2 * nsteps * nx * ny

@@ -121,8 +121,9 @@ def test_heat_adjoint_dot_product(oracle_lib):
     u = rng.standard_normal((20, 28))
     v = rng.standard_normal((20, 28))
     N = 37
-    Au = oracle_lib.heat_run(u, 0.1, N)
-    Atv = oracle_lib.heat_adjoint(v, 0.1, N)
+    dt, dx = W.heat_dt(28, 0.1)
+    Au = oracle_lib.heat_run(u, N, dt, dx)
+    Atv = oracle_lib.heat_adjoint(v, N, dt, dx)
     lhs = math.fsum((Au * v).ravel())
     rhs = math.fsum((u * Atv).ravel())
     assert abs(lhs - rhs) <= 1e-12 * math.fsum(np.abs(Au * v).ravel())
@@ -136,7 +137,8 @@ def test_heat_adjoint_closed_form(oracle_lib):
     lam = -4 * (math.sin(math.pi * 2 / n) ** 2 + math.sin(math.pi * 3 / n) ** 2)
     z = r * lam
     G = 1 + z + 0.5 * z * z
-    got = oracle_lib.heat_adjoint(mode, r, N)
+    dt, dx = W.heat_dt(n, r)
+    got = oracle_lib.heat_adjoint(mode, N, dt, dx)
     assert np.max(np.abs(got - G ** N * mode)) <= 1e-13
 
 

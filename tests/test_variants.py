@@ -45,8 +45,9 @@ def test_heat_forward_euler_is_symmetric(oracle_lib):
     """<A u, v> = <u, A v> for the App. A forward-Euler step (its own adjoint)."""
     rng = np.random.default_rng(5)
     u, v = rng.standard_normal((2, 18, 26))
-    Au = oracle_lib.heat_run(u, 0.1, 9, scheme=1)
-    Av = oracle_lib.heat_run(v, 0.1, 9, scheme=1)
+    dt, dx = W.heat_dt(26, 0.1)
+    Au = oracle_lib.heat_run(u, 9, dt, dx, scheme=1)
+    Av = oracle_lib.heat_run(v, 9, dt, dx, scheme=1)
     lhs, rhs = math.fsum((Au * v).ravel()), math.fsum((u * Av).ravel())
     assert abs(lhs - rhs) <= 1e-12 * math.fsum(np.abs(Au * v).ravel())
 
@@ -62,7 +63,7 @@ def test_heat_forward_euler_gpu(oracle_lib, nx, tile, depth, nsteps):
     dt, dx = W.heat_dt(nx, 0.2)
     s = S.Solver("heat", nx, nx, dt, dx, tile, depth, scheme=1)
     u0 = W.heat_modes(nx, nx, seed=tile + nsteps)
-    ref = oracle_lib.heat_run(u0, s.get("r"), nsteps, scheme=1)
+    ref = oracle_lib.heat_run(u0, nsteps, dt, dx, scheme=1)
     for method in ("run_swept", "run_standard"):
         u = torch.from_numpy(u0).cuda()
         getattr(s, method)(u, nsteps)
