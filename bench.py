@@ -2,15 +2,21 @@
 """Benchmark: Gcell-steps/s of the swept-rule solver against the Standard
 solver on one B300 (FP64), with the roofline of its dominant kernel.
 
-One bench step = one whole run of the workload: the isentropic vortex on a
-256 x 256 periodic grid (beta = 5, rho = p = 1, u = v = 1, gamma = 1.4, CFL
-0.25) advanced to t = 10, i.e. 2999 RK2 steps, swept block 32, depth 6
-(6 stage-levels per phase).  Inputs are seeded and synthetic and stay
-resident in device memory; L2 is flushed (a 256 MiB write) between timed
-iterations.  Prints one JSON line.
+One bench step = one whole run of the workload.  The default workload is the
+large heat problem: a 16384 x 16384 periodic grid, a seeded sum of 8 Fourier
+modes, r = 0.1, 2000 RK2 steps, swept block 64, depth 30 (30 stage-levels per
+phase).  Inputs are seeded and synthetic and stay resident in device memory;
+the state (2 GiB) and the level store (62 GiB) are far larger than L2, which
+is also flushed (a 256 MiB write) between timed iterations.  The same line
+carries the Euler vortex at 256 x 256 advanced to t = 10 (2999 steps, block
+32, depth 6), Swept against Standard, as extra keys.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload euler256|heat64|heat4096|heat16384|adjoint1024|batch256]
+                  [--workload heat16384|euler256|heat64|heat4096|adjoint1024|batch256]
+  python bench.py --peaks                      # the FP64 probe alone
+  python bench.py --workload W --ncu-run swept|standard
+        # W warm-up runs then one run, nothing timed: the command that the
+        # ncu captures summarised under profiles/ run
 
 --impl reference times the CPU oracle (the plain fp64 C reference) on the
 host cores on a bounded sample of the same workload.  Under torchrun
@@ -18,6 +24,10 @@ host cores on a bounded sample of the same workload.  Under torchrun
 exchange on one GPU.
 """
 import argparse
+import csv
+import ctypes
+import glob
+import hashlib
 import json
 import math
 import os
@@ -31,15 +41,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gcell-steps/s Swept vs Standard (FP64, 1 B300); % of HBM roofline"
 UNIT = "Gcell-steps/s"
+DEFAULT_WORKLOAD = "heat16384"
 
 # Algorithmic FP64 work per cell and stage of the arithmetic specification
 # (fma = 2 flops; add, mul, div, sqrt = 1): heat 3 adds + 2 fma = 7; Euler 187
 # (cell pressure 9, limiter 6, two faces of 76, update 20).
 FLOPS_PER_CELL_STAGE = {"heat": 7, "euler": 187}
-# FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA lanes per clock
-# (measured: 565 G FMA/s at 1.94 GHz) x 2 flops x 2032 MHz maximum SM clock.
-FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+SM_COUNT = 148
+SM_MAX_MHZ_FALLBACK = 2032.0  # B300 maximum SM clock, used when no clock was sampled
 HBM_FALLBACK_GBS = 6400.0  # used only where no measured copy bandwidth is on file
+L2_FLUSH_BYTES = 256 << 20
+CSRC = os.path.join(ROOT, "paper_2105_10332_b300", "csrc")
+TRAFFIC_CSV = os.path.join(ROOT, "profiles", "dram_per_launch.csv")
 
 
 def hbm_peak_gbs():
@@ -49,16 +62,34 @@ def hbm_peak_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return HBM_FALLBACK_GBS, "fallback"
-L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (profiles/); an entry is removed whenever that kernel changes.  The
-# 16384^2 heat Octahedron is too large to capture under the profiling size
-# rule: its entry is the 4096^2 capture scaled by the 16x windows, since at
-# both sizes the state and the level store are far larger than L2.
-HEAT4096_OCT_TRAFFIC = 652594944 + 248046080
-TRAFFIC_PER_LAUNCH = {("euler_vortex_256x256_t10", "octahedron"): 6117120 + 1280,
-                      ("heat_modes_4096x4096_200steps", "octahedron"): HEAT4096_OCT_TRAFFIC,
-                      ("heat_modes_16384x16384_2000steps", "octahedron"): 16 * HEAT4096_OCT_TRAFFIC}
+
+
+def kernel_source_digest():
+    """Digest of the library's CUDA sources and header: a traffic figure taken
+    with ncu holds only for the build it was taken on."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+    for f in files + [os.path.join(ROOT, "include", "sweep.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload_name, kernel, path=TRAFFIC_CSV):
+    """ncu DRAM bytes (read + write) of one launch of `kernel` in `workload_name`,
+    from the committed capture list, or None when there is none for the
+    current sources (the kernels changed since the counters were taken)."""
+    try:
+        with open(path, newline="") as f:
+            rows = list(csv.DictReader(f))
+    except OSError:
+        return None
+    digest = kernel_source_digest()
+    for r in rows:
+        if r["workload"] == workload_name and r["kernel"] == kernel and r["sources"] == digest:
+            return int(r["dram_read_bytes"]) + int(r["dram_write_bytes"])
+    return None
 
 
 def workload(name):
@@ -395,137 +426,260 @@ def run_adjoint(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, wl):
+def measure_fp64(dev, target_s=0.25, launches=5):
+    """The FP64 rate of this GPU from the library's fma probe (sweep_fp64_probe):
+    4 CTAs of 256 threads per SM, 8 independent chains per thread, timed
+    with CUDA events on the launching stream while nvidia-smi samples the SM
+    clock.  The roofline peak is the measured rate scaled from the sampled
+    clock to the maximum SM clock: 148 SMs x (measured fma lanes per clock and
+    SM) x 2 flops x the maximum clock."""
     import torch
     from paper_2105_10332_b300 import sweep as S
+    blocks, threads = 4 * SM_COUNT, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def launch(iters):
+        rc = S.sweep_fp64_probe(ctypes.c_void_p(out.data_ptr()), iters, blocks, threads,
+                                ctypes.c_void_p(st.cuda_stream))
+        if rc != S.SWEEP_OK:
+            raise RuntimeError("sweep_fp64_probe: status %d" % rc)
+
+    def timed(iters):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        launch(iters)
+        b.record(st)
+        return a, b
+
+    launch(1000)  # warm-up (module load)
+    a, b = timed(2000)
+    torch.cuda.synchronize(dev)
+    iters = max(2000, int(2000 * target_s * 1e3 / max(a.elapsed_time(b), 1e-3)))
+    flops = 16.0 * iters * blocks * threads
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    with sampler:
+        time.sleep(0.3)
+        evs = [timed(iters) for _ in range(launches)]
+        torch.cuda.synchronize(dev)
+    rates = sorted(flops / (x.elapsed_time(y) / 1e3) / 1e12 for x, y in evs)
+    tflops = statistics.median(rates)
+    clk = sampler.summary()
+    sm_max = clk["sm_max_mhz"] or SM_MAX_MHZ_FALLBACK
+    sm = clk["sm_mhz"] or sm_max
+    lanes = tflops * 1e12 / 2 / (SM_COUNT * sm * 1e6)
+    peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
+    return {"tflops_measured": round(tflops, 4), "sm_mhz": sm, "sm_max_mhz": sm_max,
+            "fma_lanes_per_clk_per_sm": round(lanes, 3), "peak_tflops": round(peak, 4),
+            "clock_samples": clk["samples"], "reasons": clk["reasons"],
+            "basis": "sweep_fp64_probe: %d CTAs x %d threads x 8 fma chains, median of %d "
+                     "launches; peak = 148 SMs x measured fma lanes/clk/SM x 2 flops x max SM clock"
+                     % (blocks, threads, launches)}
+
+
+class Runner:
+    """One workload's solver, device state and workspace, with each method's
+    whole run (all its launches) captured once into a CUDA graph and
+    replayed, so that host launch overhead enters neither method's timing."""
+
+    def __init__(self, wl, dev):
+        import torch
+        from paper_2105_10332_b300 import sweep as S
+        self.torch, self.wl, self.dev = torch, wl, dev
+        self.solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"],
+                               wl["depth"])
+        self.N, self.cells = wl["nsteps"], wl["nx"] * wl["ny"]
+        self.init = torch.from_numpy(wl["state"]).to(dev)
+        self.state = self.init.clone()
+        self.ws = self.solver.workspace(dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+        self.graphs = {}
+
+    def graph(self, method):
+        torch = self.torch
+        if method not in self.graphs:
+            getattr(self.solver, method)(self.state, self.N, self.ws)  # attributes set before capture
+            torch.cuda.synchronize(self.dev)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                getattr(self.solver, method)(self.state, self.N, self.ws)
+            self.graphs[method] = g
+        return self.graphs[method]
+
+    def warm(self, method, W):
+        for _ in range(W):
+            self.state.copy_(self.init)
+            self.graph(method).replay()
+        self.torch.cuda.synchronize(self.dev)
+
+    def timed(self, method, K):
+        """Total device milliseconds of K whole runs, L2 flushed before each."""
+        torch = self.torch
+        g = self.graph(method)
+        evs = []
+        for _ in range(K):
+            self.state.copy_(self.init)
+            self.flush.fill_(1)  # evict the state and level store from L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            g.replay()
+            e1.record(self.stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(self.dev)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    def profile(self):
+        """One more swept run with an event pair around each launch."""
+        self.solver.set("profile", 1)
+        self.state.copy_(self.init)
+        self.flush.fill_(1)
+        self.solver.run_swept(self.state, self.N, self.ws)
+        prof = self.solver.profile()
+        self.solver.set("profile", 0)
+        return prof
+
+
+def roofline(wl, prof, fp64):
+    """FP64-ALU roofline of the dominant kernel: its algorithmic flops per
+    launch over its live mean launch time, against the measured FP64 peak;
+    and the HBM side of the same kernel from its ncu DRAM bytes per launch."""
+    tiles = (wl["nx"] // wl["tile"]) * (wl["ny"] // wl["tile"])
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    cells = wl["nx"] * wl["ny"]
+    dom_cells = 2 * cells if dom == "standard" else shape_cells(wl["eqn"], wl["tile"], wl["depth"],
+                                                                 dom, tiles)
+    flops = dom_cells * FLOPS_PER_CELL_STAGE[wl["eqn"]]
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    traffic = traffic_per_launch(wl["name"], dom)
+    peak = fp64["peak_tflops"]
+    out = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+           "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+           "launch_ms": round(dom_ms, 5), "flops_per_launch": flops,
+           "peak_basis": "FP64, of measured (probe rate at the sampled clock scaled to the "
+                         "maximum clock)",
+           "fp64_probe": fp64,
+           "kernels": {k: {"ms_total": round(v[0], 4), "launches": v[1]} for k, v in prof.items()}}
+    if traffic is not None:
+        peak_gbs, basis = hbm_peak_gbs()
+        gbs = traffic / (dom_ms / 1e3) / 1e9
+        out["hbm"] = {"achieved": round(gbs, 2), "peak": peak_gbs, "unit": "GB/s",
+                      "frac": round(gbs / peak_gbs, 4), "peak_basis": basis}
+    return out
+
+
+def run_peaks(args):
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    print(json.dumps({"fp64_probe": measure_fp64(dev)}), flush=True)
+
+
+def run_ncu(args, wl):
+    """W eager warm-up runs and one more run of one method, nothing timed: the
+    command an ncu capture wraps (its -s skips the launches before the one
+    to capture).  Prints the launches of the last run."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = Runner(wl, dev)
+    method = "run_swept" if args.ncu_run == "swept" else "run_standard"
+    for _ in range(args.warmup):
+        r.state.copy_(r.init)
+        getattr(r.solver, method)(r.state, r.N, r.ws)
+    r.solver.set("profile", 1)
+    r.state.copy_(r.init)
+    getattr(r.solver, method)(r.state, r.N, r.ws)
+    prof = r.solver.profile()
+    print(json.dumps({"ncu_run": wl["name"], "method": args.ncu_run, "runs": args.warmup + 1,
+                      "launches_per_run": {k: v[1] for k, v in prof.items()}}), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
     rep = Replicas("nccl", dev)
-    barrier = rep.barrier
+    barrier, max_over_ranks = rep.barrier, rep.max
 
-    solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"])
-    N, cells = wl["nsteps"], wl["nx"] * wl["ny"]
-    init = torch.from_numpy(wl["state"]).to(dev)
-    state = init.clone()
-    ws = solver.workspace(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    # Each method's whole run (all its launches) is captured once into a CUDA
-    # graph on a side stream and replayed, so that host launch overhead does
-    # not enter the timing of either method.
-    graphs = {}
-
-    def graph_for(method):
-        if method not in graphs:
-            getattr(solver, method)(state, N, ws)  # kernel attributes set before capture
-            torch.cuda.synchronize(dev)
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                getattr(solver, method)(state, N, ws)
-            graphs[method] = g
-        return graphs[method]
-
-    def timed(method, K):
-        g = graph_for(method)
-        evs = []
-        for _ in range(K):
-            state.copy_(init)
-            flush.fill_(1)  # evict the state and level store from L2
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.replay()
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize(dev)
-        return sum(a.elapsed_time(b) for a, b in evs)
-
-    max_over_ranks = rep.max
+    main = Runner(wl, dev)
+    N, cells = main.N, main.cells
+    K = args.steps
+    # the Standard solver is the comparison, not the headline: it is timed on
+    # at most 3 whole runs (each run of the large heat workload is ~11 s)
+    K_std = min(K, 3)
 
     # warm-up (untimed), including the graph captures
-    for _ in range(args.warmup):
-        state.copy_(init)
-        graph_for("run_swept").replay()
-        state.copy_(init)
-        graph_for("run_standard").replay()
-    torch.cuda.synchronize(dev)
+    main.warm("run_swept", args.warmup)
+    main.warm("run_standard", 1)
 
-    # timed region: K swept runs
+    # timed region: K swept runs, clocks sampled throughout
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     barrier()
     torch.cuda.synchronize(dev)
     with sampler:
-        ms_swept = timed("run_swept", args.steps)
+        ms_swept = main.timed("run_swept", K)
         torch.cuda.synchronize(dev)
     barrier()
     ms_swept = max_over_ranks(ms_swept)
     clocks = sampler.summary()
 
-    # the Standard solver on the same workload, same protocol
     barrier()
     torch.cuda.synchronize(dev)
-    ms_std = max_over_ranks(timed("run_standard", args.steps))
+    ms_std = max_over_ranks(main.timed("run_standard", K_std))
     barrier()
 
-    # per-kernel durations: one more swept run with an event pair around each launch
-    solver.set("profile", 1)
-    state.copy_(init)
-    flush.fill_(1)
-    solver.run_swept(state, N, ws)
-    prof = solver.profile()
-    solver.set("profile", 0)
+    prof = main.profile()
     launches_per_run = sum(n for _, n in prof.values())
 
     # end to end through the public API with host buffers (pinned): H2D copy,
     # run, D2H copy inside the timed region
     host0 = torch.from_numpy(wl["state"]).pin_memory()
     host = host0.clone().pin_memory()
-    K_e2e = max(1, min(args.steps, 3))
+    K_e2e = max(1, min(K, 2))
     e2e_s = 0.0
     for _ in range(K_e2e):
         host.copy_(host0)
-        flush.fill_(1)
+        main.flush.fill_(1)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        solver.run_swept(host, N)
+        main.solver.run_swept(host, N)
         torch.cuda.synchronize(dev)
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s)
-    state_bytes = init.numel() * 8
+    state_bytes = main.init.numel() * 8
+    del host, host0
 
-    value = job_rate(world, cells, N, args.steps, ms_swept / 1e3)
-    v_std = job_rate(world, cells, N, args.steps, ms_std / 1e3)
+    value = job_rate(world, cells, N, K, ms_swept / 1e3)
+    v_std = job_rate(world, cells, N, K_std, ms_std / 1e3)
     v_e2e = job_rate(world, cells, N, K_e2e, e2e_s)
-
-    # roofline of the dominant kernel (FP64 ALU bound)
-    tiles = (wl["nx"] // wl["tile"]) * (wl["ny"] // wl["tile"])
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / prof[dom][1]
-    if dom == "standard":
-        dom_cells = 2 * cells
-    else:
-        dom_cells = shape_cells(wl["eqn"], wl["tile"], wl["depth"], dom, tiles)
-    flops = dom_cells * FLOPS_PER_CELL_STAGE[wl["eqn"]]
-    achieved = flops / (dom_ms / 1e3) / 1e12
-    traffic = TRAFFIC_PER_LAUNCH.get((wl["name"], dom))
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic,
-                "kernel": dom, "launch_ms": round(dom_ms, 5),
-                "flops_per_launch": flops, "peak_basis": "FP64 148 SMs x 2 FMA/clk x 2032 MHz (derived)",
-                "kernels": {k: {"ms_total": round(v[0], 4), "launches": v[1]} for k, v in prof.items()}}
-    # the HBM side of the same kernel: its ncu DRAM bytes per launch over the
-    # live launch time, against the copy bandwidth
-    if traffic is not None:
-        peak_gbs, basis = hbm_peak_gbs()
-        gbs = traffic / (dom_ms / 1e3) / 1e9
-        roofline["hbm"] = {"achieved": round(gbs, 2), "peak": peak_gbs, "unit": "GB/s",
-                           "frac": round(gbs / peak_gbs, 4), "peak_basis": basis}
+    fp64 = measure_fp64(dev)
+    roof = roofline(wl, prof, fp64)
 
     line = None
     if rank == 0:
+        extras = {}
+        if wl["name"] != workload("euler256")["name"]:
+            # the Euler vortex at 256^2, t = 10: Swept against Standard on the
+            # same protocol (graph replay, L2 flushed), as extra keys
+            ew = workload("euler256")
+            er = Runner(ew, dev)
+            er.warm("run_swept", 3)
+            er.warm("run_standard", 3)
+            Ke = max(1, min(K, 5))
+            es = er.timed("run_swept", Ke)
+            et = er.timed("run_standard", Ke)
+            eprof = er.profile()
+            vs = job_rate(1, er.cells, er.N, Ke, es / 1e3)
+            vt = job_rate(1, er.cells, er.N, Ke, et / 1e3)
+            eroof = roofline(ew, eprof, fp64)
+            eroof.pop("fp64_probe")
+            extras["euler256"] = {"workload": ew["name"], "runs": Ke, "swept": round(vs, 6),
+                                  "standard": round(vt, 6), "swept_over_standard": round(vs / vt, 4),
+                                  "roofline": eroof}
+            del er
         os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
         cb_value, cb_steps, cb_secs = oracle_sample(wl, 12.0)
         cpu_baseline = {"value": round(cb_value, 6), "unit": UNIT,
@@ -533,22 +687,25 @@ def run_ours(args, wl):
                         "sample": "%d RK2 steps of the same workload (%d-step runs from its "
                                   "initial state), %.1f s" % (cb_steps, N, cb_secs)}
         line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(ms_swept / args.steps, 3), "higher_is_better": True,
+                "steps": K, "warmup": args.warmup,
+                "ms_per_step": round(ms_swept / K, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic (seeded isentropic vortex / heat modes)",
+                "data": "synthetic (seeded heat modes / isentropic vortex)",
                 "config": {"workload": wl["name"], "nx": wl["nx"], "ny": wl["ny"],
                            "steps_per_run": N, "tile": wl["tile"], "depth": wl["depth"],
-                           "standard_tile": int(solver.get("standard_tile")),
-                           "l2": "flushed (256 MiB write) between timed iterations",
+                           "standard_tile": int(main.solver.get("standard_tile")),
+                           "l2": "inputs larger than L2, and flushed (256 MiB write) between "
+                                 "timed iterations",
                            "launch": "each run captured once into a CUDA graph and replayed",
+                           "standard_runs_timed": K_std, "e2e_runs": K_e2e,
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "standard": {"value": round(v_std, 6), "ms_per_step": round(ms_std / args.steps, 3)},
+                "standard": {"value": round(v_std, 6), "ms_per_step": round(ms_std / K_std, 3)},
                 "swept_over_standard": round(value / v_std, 4),
                 "e2e": {"value": round(v_e2e, 6), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes},
-                "gpu_launches": int(launches_per_run * args.steps),
-                "roofline": roofline, "cpu_baseline": cpu_baseline, "clocks": clocks}
+                "gpu_launches": int(launches_per_run * K),
+                "roofline": roof, "cpu_baseline": cpu_baseline, "clocks": clocks}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     rep.close()
 
@@ -559,13 +716,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="euler256")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--peaks", action="store_true")
+    ap.add_argument("--ncu-run", choices=["swept", "standard"], default=None)
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
+    if args.peaks:
+        run_peaks(args)
+        return
+    if args.warmup < 3 and args.impl == "ours" and args.ncu_run is None:
         args.warmup = 3
     wl = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.ncu_run:
+        run_ncu(args, wl)
     elif wl.get("adjoint"):
         run_adjoint(args, wl)
     elif wl.get("batch"):

@@ -227,6 +227,18 @@ int sweep_run_swept_static(sweep_t *h, double *d_state, int64_t nsteps,
  */
 int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds);
 
+/*
+ * FP64 throughput probe (a measuring instrument, not part of the method):
+ * launches `blocks` CTAs of `threads` threads on the stream; every thread
+ * takes 8 independent chains of `iters` fused multiply-adds and writes one
+ * double to d_out[blocks * threads] (device, caller-owned).  The launch does
+ * 16 * iters * blocks * threads flops (an fma counts 2); timed with events on
+ * the stream it gives the FP64 rate that bounds the swept kernels.
+ * Returns SWEEP_EINVAL for threads not a multiple of 32 in [32, 1024].
+ */
+int sweep_fp64_probe(double *d_out, int64_t iters, int blocks, int threads,
+                     struct CUstream_st *stream);
+
 /* Release a handle (NULL is ignored). */
 void sweep_destroy(sweep_t *h);
 

@@ -616,6 +616,36 @@ struct BatchPool {
 BatchPool batch_pool[kMaxBatchDevices];
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Create the pool's streams and events.  On a failure everything created so
+// far is destroyed again and the pool stays not ready, so a later call
+// starts over instead of leaking or reusing half a pool.
+int make_batch_pool(BatchPool *bp)
+{
+    cudaStream_t s[kBatchStreams] = {};
+    cudaEvent_t done[kBatchStreams] = {}, fork = nullptr;
+    int ns = 0, ne = 0;
+    bool ok = true;
+    for (int k = 0; k < kBatchStreams && ok; ++k) {
+        ok = cudaStreamCreateWithFlags(&s[k], cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) ++ns;
+        ok = ok && cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) == cudaSuccess;
+        if (ok) ++ne;
+    }
+    ok = ok && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (int k = 0; k < ne; ++k) cudaEventDestroy(done[k]);
+        for (int k = 0; k < ns; ++k) cudaStreamDestroy(s[k]);
+        return SWEEP_ECUDA;
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        bp->s[k] = s[k];
+        bp->done[k] = done[k];
+    }
+    bp->fork = fork;
+    bp->ready = true;
+    return SWEEP_OK;
+}
 }  // namespace
 
 SWEEP_API size_t sweep_batch_workspace_bytes(sweep_t *const *hs, int count)
@@ -644,13 +674,8 @@ SWEEP_API int sweep_batch_run(sweep_t *const *hs, double *const *d_states, const
     {
         std::lock_guard<std::mutex> lock(batch_mu);
         if (!bp->ready) {
-            for (int k = 0; k < kBatchStreams; ++k)
-                if (cudaStreamCreateWithFlags(&bp->s[k], cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&bp->done[k], cudaEventDisableTiming) != cudaSuccess)
-                    return SWEEP_ECUDA;
-            if (cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) != cudaSuccess)
-                return SWEEP_ECUDA;
-            bp->ready = true;
+            const int rc = make_batch_pool(bp);
+            if (rc != SWEEP_OK) return rc;
         }
     }
     // largest work first, dealt round-robin over the streams

@@ -40,6 +40,7 @@ SIGNATURES = {
                                  _c_int, _vp, _vp]),
     "sweep_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _c_i64, _c_int, _vp, _vp]),
     "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
+    "sweep_fp64_probe": (_c_int, [_vp, _c_i64, _c_int, _c_int, _vp]),
     "sweep_destroy": (None, [_vp]),
     "sweep_error_string": (ctypes.c_char_p, [_c_int]),
 }
@@ -130,6 +131,11 @@ def sweep_profile_read(h, nkinds=5):
     n = (ctypes.c_int64 * nkinds)()
     _check(lib().sweep_profile_read(h, ms, n, int(nkinds)), "sweep_profile_read")
     return list(ms), list(n)
+
+
+def sweep_fp64_probe(out_ptr, iters, blocks, threads, stream_ptr):
+    """Enqueue the FP64 fma-throughput probe (16 * iters * blocks * threads flops)."""
+    return int(lib().sweep_fp64_probe(out_ptr, int(iters), int(blocks), int(threads), stream_ptr))
 
 
 def sweep_destroy(h):

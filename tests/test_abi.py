@@ -135,6 +135,34 @@ def test_autotune_candidates_are_legal():
     assert autotune.size_class(96) == 128 and autotune.size_class(64) == 64
 
 
+def test_autotuner_gives_every_batch_side_a_legal_config():
+    """The 256 sides of the batched workload (multiples of 32 in [64, 2048]),
+    both equations: a size class first tuned on a side that admits tile 64
+    (e.g. 384) must not hand tile 64 to a later side of the class it does not
+    divide (e.g. 352).  The timer is a stand-in that prefers the largest tile
+    and cannot build one configuration in three; no GPU is used."""
+    from paper_2105_10332_b300 import autotune, workloads as W
+    calls = []
+
+    def measure(cfg):
+        calls.append(cfg)
+        if (cfg["tile"] + cfg["depth"]) % 3 == 0:
+            return None
+        return 100.0 / cfg["tile"] + 0.01 * cfg["depth"]
+
+    tuner = autotune.Autotuner()
+    sides = W.batch_sides(256)
+    for k, side in enumerate(sides):
+        eqn = "heat" if k % 2 == 0 else "euler"
+        cfg = tuner.select(eqn, side, measure)
+        assert cfg in autotune.candidates(eqn, side), (eqn, side, cfg)
+        assert side % cfg["tile"] == 0 and side // cfg["tile"] >= 2
+    assert None not in tuner.cache.values()
+    assert len(calls) < 4 * len(sides)  # classes reuse their ranking
+    with pytest.raises(RuntimeError):
+        autotune.Autotuner().select("heat", 384, lambda cfg: None)
+
+
 def test_batch_workspace_is_sum_of_instances(L):
     hs = [S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6),
           S.sweep_create(S.SWEEP_EULER, 96, 96, 1e-3, 0.1, 32, 6)]

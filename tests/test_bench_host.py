@@ -40,3 +40,24 @@ def test_hbm_peak_prefers_the_measured_value(tmp_path, monkeypatch):
     assert bench.hbm_peak_gbs() == (bench.HBM_FALLBACK_GBS, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6502.2}))
     assert bench.hbm_peak_gbs() == (6502.2, "measured")
+
+
+def test_traffic_needs_a_capture_of_the_current_sources(tmp_path):
+    """A DRAM traffic figure is used only if it was captured on the kernel
+    sources as they stand: any other digest reads as no figure (null)."""
+    import bench
+    path = tmp_path / "dram.csv"
+    digest = bench.kernel_source_digest()
+    path.write_text("workload,kernel,dram_read_bytes,dram_write_bytes,sources,command\n"
+                    "heat_x,octahedron,100,28,%s,ncu ...\n"
+                    "heat_x,bridges,7,1,0123456789abcdef,ncu ...\n" % digest)
+    assert bench.traffic_per_launch("heat_x", "octahedron", str(path)) == 128
+    assert bench.traffic_per_launch("heat_x", "bridges", str(path)) is None
+    assert bench.traffic_per_launch("heat_y", "octahedron", str(path)) is None
+    assert bench.traffic_per_launch("heat_x", "octahedron", str(tmp_path / "none.csv")) is None
+    assert len(digest) == 16 and digest == bench.kernel_source_digest()
+
+
+def test_default_workload_is_the_large_heat_grid():
+    import bench
+    assert bench.DEFAULT_WORKLOAD == "heat16384"
