@@ -12,7 +12,7 @@ carries the Euler vortex at 256 x 256 advanced to t = 10 (2999 steps, block
 32, depth 6), Swept against Standard, as extra keys.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload heat16384|euler256|heat64|heat4096|adjoint1024|batch256]
+                  [--workload heat16384|euler256|euler1024|heat64|heat4096|adjoint1024|batch256]
   python bench.py --peaks                      # the FP64 probe alone
   python bench.py --workload W --ncu-run swept|standard
         # W warm-up runs then one run, nothing timed: the command that the
@@ -99,6 +99,12 @@ def workload(name):
         dt, N = W.vortex_dt(q0, dx, 10.0, cfl=0.25)
         return dict(name="euler_vortex_256x256_t10", eqn="euler", nx=256, ny=256, dt=dt, dx=dx,
                     nsteps=N, tile=32, depth=6, state=q0)
+    if name == "euler1024":
+        # a larger vortex grid for the DRAM-bytes comparison (state 32 MiB)
+        q0, dx = W.vortex(1024)
+        dt, _ = W.vortex_dt(q0, dx, 10.0, cfl=0.25)
+        return dict(name="euler_vortex_1024x1024_120steps", eqn="euler", nx=1024, ny=1024, dt=dt,
+                    dx=dx, nsteps=120, tile=32, depth=6, state=q0)
     if name == "heat64":
         dt, dx = W.heat_dt(64, 0.1)
         return dict(name="heat_sine_64x64_500steps", eqn="heat", nx=64, ny=64, dt=dt, dx=dx,

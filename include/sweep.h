@@ -32,6 +32,15 @@
  *     its comment says so, so the enqueued sequence can be captured into a
  *     CUDA graph.
  *   - Errors: a nonzero sweep_status; nothing aborts, exits or traps.
+ *     Argument and launch errors are returned at once.  What the kernels
+ *     find while they run goes to a device error word, the first 4 bytes
+ *     of the workspace header, which every run clears on entry: bit
+ *     SWEEP_DEV_LAUNCH (a kernel found its grid, block or shared memory
+ *     wrong for its geometry; it then does nothing) and bit
+ *     SWEEP_DEV_NONFINITE (a state value written to the state array was an
+ *     infinity or a NaN, e.g. after a time step beyond the CFL bound).
+ *     sweep_check reads it; with the "check" parameter set every run reads
+ *     it before returning (and so waits for the GPU).
  *   - Threads: one handle must not be used from two threads at once;
  *     separate handles are independent.
  */
@@ -56,9 +65,17 @@ enum sweep_status {
     SWEEP_EINVAL = 1,      /* bad argument or geometry                       */
     SWEEP_ENOMEM = 2,      /* host allocation failed                         */
     SWEEP_ECUDA = 3,       /* a CUDA call or kernel launch failed            */
-    SWEEP_ETIMEOUT = 4,    /* a bounded device-side wait gave up             */
-    SWEEP_EUNSUPPORTED = 5 /* valid request that this build does not handle  */
+    SWEEP_ETIMEOUT = 4,    /* reserved for a bounded device-side wait that gives
+                              up; no kernel of this build waits on another CTA
+                              (clusters use the hardware cluster barrier), so no
+                              call returns it                                 */
+    SWEEP_EUNSUPPORTED = 5, /* valid request that this build does not handle */
+    SWEEP_EDEVICE = 6      /* the device error word was set (sweep_check)    */
 };
+
+/* bits of the device error word */
+#define SWEEP_DEV_LAUNCH 1u
+#define SWEEP_DEV_NONFINITE 2u
 
 /*
  * Create a solver for an nx x ny periodic grid.
@@ -102,6 +119,11 @@ int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile
  *   "profile"        1: every later run brackets each kernel launch with a
  *                    pair of CUDA events on its stream (read them with
  *                    sweep_profile_read); 0 (default): no events
+ *   "check"          1: every run (swept, standard, adjoint, static) ends
+ *                    by waiting for its stream and reading the device error
+ *                    word, and returns SWEEP_EDEVICE if a bit is set (the
+ *                    run is then not capturable into a CUDA graph); 0
+ *                    (default): runs stay asynchronous
  * Returns SWEEP_EINVAL for an unknown key or a value out of range.
  */
 int sweep_set_param(sweep_t *h, const char *key, double value);
@@ -238,6 +260,40 @@ int sweep_profile_read(sweep_t *h, double *ms, int64_t *launches, int nkinds);
  */
 int sweep_fp64_probe(double *d_out, int64_t iters, int blocks, int threads,
                      struct CUstream_st *stream);
+
+/*
+ * Wait for `stream`, read the device error word of the workspace d_ws (the
+ * workspace of the runs to check, 256-byte aligned), store it in *bits (if
+ * bits is not NULL) and clear it.  Returns SWEEP_OK when no bit was set,
+ * SWEEP_EDEVICE when one was, SWEEP_ECUDA if the wait or the copy failed.
+ * Synchronous.  For a batch, each instance's word heads its own region of
+ * the batch workspace.
+ */
+int sweep_check(const void *d_ws, unsigned *bits, struct CUstream_st *stream);
+
+/*
+ * Test hooks: host-side fault injection.  sweep_inject_fault(site, n) makes
+ * the n-th next pass through `site` fail the way the real failure would
+ * (n = 0, or site 0, disarms):
+ *   SWEEP_SITE_HOST_ALLOC   the handle allocation of sweep_create
+ *                           (sweep_create returns SWEEP_ENOMEM)
+ *   SWEEP_SITE_STREAM_POOL  creating a stream or an event of the batch
+ *                           pool (sweep_batch_run returns SWEEP_ECUDA and
+ *                           destroys what it had created)
+ *   SWEEP_SITE_EVENTS       creating a profiling event pair (that launch is
+ *                           not timed)
+ * Nothing here makes a GPU fault.  The setting is process-wide; returns
+ * SWEEP_EINVAL for an unknown site or a negative n.
+ * sweep_live_cuda_objects() counts the CUDA streams and events the library
+ * holds (the batch pools and the profiling events of live handles).
+ */
+enum sweep_fault_site {
+    SWEEP_SITE_HOST_ALLOC = 1,
+    SWEEP_SITE_STREAM_POOL = 2,
+    SWEEP_SITE_EVENTS = 3
+};
+int sweep_inject_fault(int site, int nth);
+int sweep_live_cuda_objects(void);
 
 /* Release a handle (NULL is ignored). */
 void sweep_destroy(sweep_t *h);

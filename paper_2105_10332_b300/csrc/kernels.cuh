@@ -103,7 +103,48 @@ struct Params {
     // in a swept run, so the arrays end up complete.
     double *hist_q, *hist_qs;
     int64_t hist_stride, hist_levels;
+    // Device error word (the first 4 bytes of the workspace header), or null:
+    // kernels OR in the kErr* bits below; the host reads it with sweep_check.
+    unsigned *err;
 };
+
+// Bits of the device error word.
+constexpr unsigned kErrLaunch = 1u;     // a kernel found its launch geometry or shared memory wrong
+constexpr unsigned kErrNonFinite = 2u;  // a state value written was an infinity or a NaN
+
+__device__ __forceinline__ void report(const Params &p, unsigned bit)
+{
+    if (p.err)
+        atomicOr(p.err, bit);
+}
+
+// bytes of dynamic shared memory this launch was given
+__device__ __forceinline__ unsigned dyn_smem_bytes()
+{
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// Launch check at kernel entry: the grid, the block and the shared memory the
+// kernel's geometry needs.  The condition is the same for every CTA of the
+// launch, so when it fails every CTA returns before any barrier (nothing
+// waits on a CTA that left), and CTA 0 reports it.
+__device__ __forceinline__ bool launch_ok(const Params &p, unsigned grid, unsigned threads,
+                                          size_t smem)
+{
+    const bool ok = gridDim.x == grid && blockDim.x == threads && dyn_smem_bytes() >= smem;
+    if (!ok && blockIdx.x == 0 && threadIdx.x == 0)
+        report(p, kErrLaunch);
+    return ok;
+}
+
+// an infinity or a NaN, by the bit pattern (integer pipe only)
+__device__ __forceinline__ bool nonfinite(double v)
+{
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) ==
+           0x7ff0000000000000ull;
+}
 
 // ------------------------------------------------------------------ equations
 
@@ -152,18 +193,27 @@ __host__ __device__ constexpr size_t euler_scratch(int wp, int C)
            (size_t)4 * r * (wp - 3) + (size_t)4 * (r + 1) * (wp - 4);
 }
 
-// shared-memory bytes of one CTA with window edge wp
+// shared-memory bytes of one CTA with window edge wp (a one-component
+// equation's odd-level buffer starts one double late, see Block::carve)
 template <class EQ>
 __host__ __device__ constexpr size_t smem_bytes(int wp, int C)
 {
     if (EQ::NC == 1)
-        return sizeof(double) * 2 * (size_t)wp * wp;
+        return sizeof(double) * (2 * (size_t)wp * wp + 2);
     return sizeof(double) * ((size_t)8 * wp * wp + euler_scratch(wp, C));
 }
 
 // Per-CTA view of shared memory.
+//
+// Level-store traffic moves in 16-byte pairs of cells (x, x+1) whose global
+// x is even (one row of a 2 x 2 block of the store).  For a radius-1
+// equation the store's block grid is shifted by one cell on odd levels, so
+// the pairs of an odd level start on odd window columns; buffer H then
+// starts one double late (kHoff), which puts those pairs on 16-byte
+// boundaries of shared memory as well.
 template <class EQ, int C>
 struct Block {
+    static constexpr int kHoff = EQ::N == 1 ? 1 : 0;
     double *buf[2];               // F (even levels), H (odd levels): [NC][wp*wp]
     double *peer[C > 1 ? C : 1];  // Euler/heat: base of each peer's shared buffer (C > 1)
     double *P, *hxp, *hxm, *hyp, *hym, *fx, *fy;  // Euler scratch
@@ -180,7 +230,7 @@ struct Block {
         wp = wp_;
         plane = wp * wp;
         buf[0] = smem;
-        buf[1] = smem + EQ::NC * plane;
+        buf[1] = smem + EQ::NC * plane + kHoff;
         rank = 0;
         if constexpr (C > 1) {
             cg::cluster_group cl = cg::this_cluster();
@@ -210,7 +260,7 @@ struct Block {
     // this CTA's copy and every peer's
     __device__ __forceinline__ void put(int64_t level, int c, int i, double v)
     {
-        const int off = (int)(level & 1) * EQ::NC * plane + c * plane + i;
+        const int off = (int)(level & 1) * (EQ::NC * plane + kHoff) + c * plane + i;
         buf[0][off] = v;
         if constexpr (C > 1) {
 #pragma unroll
@@ -240,47 +290,57 @@ __device__ __forceinline__ int64_t gidx(const Params &p, int64_t ox, int64_t oy,
     return gy * p.nx + gx;
 }
 
-// Visit every cell of O \ I (I inside O or empty) with the CTA's threads,
-// packed linearly so that no lane idles while work is left.
+// Visit O \ I (I inside O or empty) with the CTA's threads, packed linearly
+// so that no lane idles while work is left, in units: where a part of O \ I
+// starts on a window column x = par (mod 2) and is an even number of cells
+// wide, and vec is set, a unit is the pair of cells (x, x+1) (f gets
+// two = true); elsewhere a unit is one cell.  O \ I is taken as the parts
+// below I, above I (full width), left of I and right of I.
 template <class F>
-__device__ __forceinline__ void for_diff(Rect O, Rect I, F &&f)
+__device__ __forceinline__ void for_units(Rect O, Rect I, int par, bool vec, F &&f)
 {
     if (O.empty())
         return;
-    if (I.empty()) {
-        const int w = O.w(), total = O.area();
-        for (int q = threadIdx.x; q < total; q += blockDim.x)
-            f(O.x0 + q % w, O.y0 + q / w);
-        return;
+    Rect a = O, b = {0, 0, 0, 0}, c = {0, 0, 0, 0}, e = {0, 0, 0, 0};
+    if (!I.empty()) {
+        a = {O.x0, O.x1, O.y0, I.y0};
+        b = {O.x0, O.x1, I.y1, O.y1};
+        c = {O.x0, I.x0, I.y0, I.y1};
+        e = {I.x1, O.x1, I.y0, I.y1};
     }
-    // below I, above I (full width), left of I, right of I
-    const int wo = O.w();
-    const int a0 = wo * (I.y0 - O.y0);
-    const int a1 = a0 + wo * (O.y1 - I.y1);
-    const int wl = I.x0 - O.x0, wr = O.x1 - I.x1, hi = I.h();
-    const int a2 = a1 + wl * hi;
-    const int total = a2 + wr * hi;
+    auto pairs = [&](const Rect &R) {
+        return vec && !R.empty() && ((R.x0 - par) & 1) == 0 && (R.w() & 1) == 0;
+    };
+    const bool ta = pairs(a), tb = pairs(b), tc = pairs(c), te = pairs(e);
+    const int wa = ta ? a.w() >> 1 : a.w(), wb = tb ? b.w() >> 1 : b.w();
+    const int wc = tc ? c.w() >> 1 : c.w(), we = te ? e.w() >> 1 : e.w();
+    const int s1 = wa * a.h(), s2 = s1 + wb * b.h(), s3 = s2 + wc * c.h();
+    const int total = s3 + we * e.h();
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        // the branches pick coordinates only: f has one call site, so a warp
-        // whose lanes fall in different parts still runs its body once
+        // the branches pick coordinates only: f has one call site
         int x, y;
-        if (q < a0) {
-            x = O.x0 + q % wo;
-            y = O.y0 + q / wo;
-        } else if (q < a1) {
-            const int r = q - a0;
-            x = O.x0 + r % wo;
-            y = I.y1 + r / wo;
-        } else if (q < a2) {
-            const int r = q - a1;
-            x = O.x0 + r % wl;
-            y = I.y0 + r / wl;
+        bool two;
+        if (q < s1) {
+            x = a.x0 + (q % wa) * (ta ? 2 : 1);
+            y = a.y0 + q / wa;
+            two = ta;
+        } else if (q < s2) {
+            const int r = q - s1;
+            x = b.x0 + (r % wb) * (tb ? 2 : 1);
+            y = b.y0 + r / wb;
+            two = tb;
+        } else if (q < s3) {
+            const int r = q - s2;
+            x = c.x0 + (r % wc) * (tc ? 2 : 1);
+            y = c.y0 + r / wc;
+            two = tc;
         } else {
-            const int r = q - a2;
-            x = I.x1 + r % wr;
-            y = I.y0 + r / wr;
+            const int r = q - s3;
+            x = e.x0 + (r % we) * (te ? 2 : 1);
+            y = e.y0 + r / we;
+            two = te;
         }
-        f(x, y);
+        f(x, y, two);
     }
 }
 
@@ -318,8 +378,14 @@ __device__ __forceinline__ int64_t sidx(const Params &p, int64_t ox, int64_t oy,
     return (((gy >> 1) * (p.nx >> 1) + (gx >> 1)) << 2) + ((gy & 1) << 1) + (gx & 1);
 }
 
-// 8-byte asynchronous global -> shared copy (cp.async), and the wait for all
-// of this thread's outstanding copies
+// Asynchronous global -> shared copies (cp.async): 16 bytes cached in L2
+// only (.cg), or 8 bytes; and the wait for all of this thread's copies.
+// Both addresses of a 16-byte copy are 16-byte aligned.
+__device__ __forceinline__ void cp_async16(double *smem_dst, const double *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async8(double *smem_dst, const double *gsrc)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -330,7 +396,21 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// level-store traffic of one CTA (loads go to this CTA's copy only)
+// copy one unit of for_units (two cells when `two`, both addresses 16-byte
+// aligned; else one) between two places with plain loads and stores
+__device__ __forceinline__ void copy_unit(double *dst, const double *src, bool two)
+{
+    if (two)
+        *reinterpret_cast<double2 *>(dst) = *reinterpret_cast<const double2 *>(src);
+    else
+        *dst = *src;
+}
+
+// Level-store traffic of one CTA (loads go to this CTA's copy only).  A
+// piece's pairs start on the global column parity of the store's blocks,
+// i.e. window column (ox + shift) mod 2; they are 16-byte aligned in shared
+// memory when the window origin ox is even (always, for a block edge that
+// is a multiple of 4; an odd origin takes the 8-byte path).
 template <class EQ, int C>
 __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &B, int64_t level,
                                                  Rect O, Rect I)
@@ -339,11 +419,17 @@ __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &
     double *dst = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
-    for_diff(O, I, [&](int x, int y) {
+    const int par = (int)((B.ox + shift) & 1);
+    for_units(O, I, par, (B.ox & 1) == 0, [&](int x, int y, bool two) {
         const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            cp_async8(dst + c * B.plane + y * B.wp + x, src + c * gplane + g);
+        for (int c = 0; c < EQ::NC; ++c) {
+            double *d = dst + c * B.plane + y * B.wp + x;
+            if (two)
+                cp_async16(d, src + c * gplane + g);
+            else
+                cp_async8(d, src + c * gplane + g);
+        }
     });
 }
 
@@ -355,12 +441,45 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
     const double *src = B.buf[level & 1];
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
-    for_diff(O, I, [&](int x, int y) {
+    const int par = (int)((B.ox + shift) & 1);
+    for_units(O, I, par, (B.ox & 1) == 0, [&](int x, int y, bool two) {
         const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
-            dst[c * gplane + g] = src[c * B.plane + y * B.wp + x];
+            copy_unit(dst + c * gplane + g, src + c * B.plane + y * B.wp + x, two);
     });
+}
+
+// A whole rectangle R of the window between the row-major state (global,
+// periodic) and buffer `buf` of shared memory, in 16-byte pairs of cells
+// (x, x+1), x even, where the window origin is even and the buffer has no
+// one-double offset (a pair never straddles the periodic seam: nx is even);
+// one cell at a time otherwise.  to_smem: state -> shared memory, else
+// shared memory -> state.
+template <class EQ, int C>
+__device__ __forceinline__ void state_rect(const Params &p, Block<EQ, C> &B, double *state, int buf,
+                                           Rect R, bool to_smem)
+{
+    const int64_t gplane = p.nx * p.ny;
+    double *sm = B.buf[buf];
+    const bool vec = (B.ox & 1) == 0 && (buf == 0 || Block<EQ, C>::kHoff == 0);
+    bool bad = false;
+    for_units(R, Rect{0, 0, 0, 0}, 0, vec, [&](int x, int y, bool two) {
+        const int64_t g = gidx(p, B.ox, B.oy, x, y);
+#pragma unroll
+        for (int c = 0; c < EQ::NC; ++c) {
+            double *s = sm + c * B.plane + y * B.wp + x;
+            double *d = state + c * gplane + g;
+            if (to_smem) {
+                copy_unit(s, d, two);
+            } else {
+                copy_unit(d, s, two);
+                bad = bad || nonfinite(s[0]) || (two && nonfinite(s[1]));
+            }
+        }
+    });
+    if (bad)
+        report(p, kErrNonFinite);
 }
 
 // -------------------------------------------------------------- stage kernels
@@ -738,20 +857,17 @@ __device__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 template <class EQ, int C>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
+    const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
+    if (!launch_ok(p, tiles * C, EQ::SWEPT_THREADS, smem_bytes<EQ>(p.b, C * p.passes)))
+        return;
     Block<EQ, C> B;
     B.carve(smem, p.b, p.passes);
     const int t = blockIdx.x / C;
     const int I = t % p.tiles_x, J = t / p.tiles_x;
     B.ox = (int64_t)I * p.b;
     B.oy = (int64_t)J * p.b;
-    const int64_t gplane = p.nx * p.ny;
-    for_rect({0, p.b, 0, p.b}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            B.buf[0][c * B.plane + y * B.wp + x] = p.state[c * gplane + g];
-    });
+    state_rect(p, B, p.state, 0, Rect{0, p.b, 0, p.b}, true);
     level_barrier<C>();  // also: every CTA of the cluster has started
     run_pyramid<EQ, C>(p, B, 0);
     level_barrier<C>();  // no CTA leaves while a peer may still write to it
@@ -762,7 +878,10 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
 template <class EQ, int C>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t base, int o)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
+    const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
+    if (!launch_ok(p, 2 * tiles * C, EQ::SWEPT_THREADS, smem_bytes<EQ>(p.b, C * p.passes)))
+        return;
     Block<EQ, C> B;
     B.carve(smem, p.b, p.passes);
     const int sh = blockIdx.x / C;
@@ -786,7 +905,10 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t
 template <class EQ, int C>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int64_t base, int o, int last)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
+    const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
+    if (!launch_ok(p, tiles * C, EQ::SWEPT_THREADS, smem_bytes<EQ>(p.b, C * p.passes)))
+        return;
     Block<EQ, C> B;
     B.carve(smem, p.b, p.passes);
     const int t = blockIdx.x / C;
@@ -804,14 +926,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int6
     if (!last) {
         run_pyramid<EQ, C>(p, B, top);
     } else {
-        const int64_t gplane = p.nx * p.ny;
-        const double *src = B.buf[top & 1];
-        for_rect(band(whole, B.rank, C), [&](int x, int y) {
-            const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-            for (int c = 0; c < EQ::NC; ++c)
-                p.state[c * gplane + g] = src[c * B.plane + y * B.wp + x];
-        });
+        state_rect(p, B, p.state, (int)(top & 1), band(whole, B.rank, C), false);
     }
     if constexpr (C > 1) cg::this_cluster().sync();
 }
@@ -824,39 +939,26 @@ template <class EQ>
 __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(Params p, const double *src, double *dst,
                                                        double *qstar)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 4 * n;
+    if (!launch_ok(p, (unsigned)((p.nx / T) * (p.ny / T)), EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
+        return;
     Block<EQ, 1> B;
     B.carve(smem, wp);
     const int tx = (int)(p.nx / T);
     const int I = blockIdx.x % tx, J = blockIdx.x / tx;
     B.ox = (int64_t)I * T - 2 * n;
     B.oy = (int64_t)J * T - 2 * n;
-    const int64_t gplane = p.nx * p.ny;
-    for_rect({0, wp, 0, wp}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            B.buf[0][c * B.plane + y * wp + x] = src[c * gplane + g];
-    });
+    state_rect(p, B, const_cast<double *>(src), 0, Rect{0, wp, 0, wp}, true);
     __syncthreads();
     Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
+    const Rect tile = {2 * n, wp - 2 * n, 2 * n, wp - 2 * n};
     if (qstar)
-        for_rect({2 * n, wp - 2 * n, 2 * n, wp - 2 * n}, [&](int x, int y) {
-            const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-            for (int c = 0; c < EQ::NC; ++c)
-                qstar[c * gplane + g] = B.buf[1][c * B.plane + y * wp + x];
-        });
-    Stage<EQ, 1>::run(p, B, 2, {2 * n, wp - 2 * n, 2 * n, wp - 2 * n});
+        state_rect(p, B, qstar, 1, tile, false);
+    Stage<EQ, 1>::run(p, B, 2, tile);
     __syncthreads();
-    for_rect({2 * n, wp - 2 * n, 2 * n, wp - 2 * n}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            dst[c * gplane + g] = B.buf[0][c * B.plane + y * wp + x];
-    });
+    state_rect(p, B, dst, 0, tile, false);
 }
 
 // One level on every cell (tiles of std_tile with a halo of n): the first
@@ -864,30 +966,21 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(Params p, const do
 template <class EQ>
 __global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(Params p, const double *src, double *dst)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 2 * n;
+    if (!launch_ok(p, (unsigned)((p.nx / T) * (p.ny / T)), EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
+        return;
     Block<EQ, 1> B;
     B.carve(smem, wp);
     const int tx = (int)(p.nx / T);
     const int I = blockIdx.x % tx, J = blockIdx.x / tx;
     B.ox = (int64_t)I * T - n;
     B.oy = (int64_t)J * T - n;
-    const int64_t gplane = p.nx * p.ny;
-    for_rect({0, wp, 0, wp}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            B.buf[0][c * B.plane + y * wp + x] = src[c * gplane + g];
-    });
+    state_rect(p, B, const_cast<double *>(src), 0, Rect{0, wp, 0, wp}, true);
     __syncthreads();
     Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
-    for_rect({n, wp - n, n, wp - n}, [&](int x, int y) {
-        const int64_t g = gidx(p, B.ox, B.oy, x, y);
-#pragma unroll
-        for (int c = 0; c < EQ::NC; ++c)
-            dst[c * gplane + g] = B.buf[1][c * B.plane + y * wp + x];
-    });
+    state_rect(p, B, dst, 1, Rect{n, wp - n, n, wp - n}, false);
 }
 
 }  // namespace sweep

@@ -2,6 +2,7 @@
 // workspace sizing and the launch sequences of the Swept and Standard solvers.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -27,6 +28,7 @@ struct sweep_s {
     int cluster;     // CTAs per Up-Pyramid / Octahedron window (1, 2 or 4)
     int cluster_br;  // CTAs per Bridge window (1, 2 or 4)
     int passes;      // sub-bands per CTA and level (1, 2 or 4)
+    int check;       // 1: every run ends by reading the device error word (synchronous)
     // optional per-launch event timing ("profile" parameter)
     int profile;
     std::vector<cudaEvent_t> ev;   // start/end pairs, reused across runs
@@ -36,7 +38,21 @@ struct sweep_s {
 
 namespace {
 
-constexpr size_t kHeader = 256;
+constexpr size_t kHeader = 256;  // workspace header: the device error word, then padding
+
+// ---- host-side fault injection (test hooks; nothing here touches a GPU)
+std::atomic<int> fault_site{0};   // armed site, 0 = none
+std::atomic<int> fault_count{0};  // passes through the site left before the failure
+std::atomic<int> live_objects{0};  // CUDA streams and events the library holds
+
+// true on the pass through `site` that was armed to fail (then disarms)
+bool inject(int site)
+{
+    if (fault_site.load() != site) return false;
+    if (fault_count.fetch_sub(1) != 1) return false;
+    fault_site.store(0);
+    return true;
+}
 
 int radius(int eqn) { return eqn == SWEEP_HEAT ? 1 : 2; }
 int ncomp(int eqn) { return eqn == SWEEP_HEAT ? 1 : 4; }
@@ -104,6 +120,7 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     p.hist_qs = nullptr;
     p.hist_stride = 0;
     p.hist_levels = 0;
+    p.err = ws ? (unsigned *)ws : nullptr;
     return p;
 }
 
@@ -129,7 +146,7 @@ struct Bracket {
         i = h->ev_used;
         if (2 * (i + 1) > h->ev.size()) {
             cudaEvent_t a, b;
-            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (inject(SWEEP_SITE_EVENTS) || cudaEventCreate(&a) != cudaSuccess) return;
             if (cudaEventCreate(&b) != cudaSuccess) {
                 cudaEventDestroy(a);
                 return;
@@ -137,6 +154,7 @@ struct Bracket {
             h->ev.push_back(a);
             h->ev.push_back(b);
             h->ev_kind.push_back(kind);
+            live_objects += 2;
         }
         h->ev_kind[i] = kind;
         on = cudaEventRecord(h->ev[2 * i], st) == cudaSuccess;
@@ -412,6 +430,31 @@ int check_run(const sweep_t *h, const double *state, int64_t nsteps, const void 
     return SWEEP_OK;
 }
 
+// clear the device error word before a run's kernels
+int clear_error_word(void *ws, cudaStream_t st)
+{
+    return cudaMemsetAsync(ws, 0, sizeof(unsigned), st) == cudaSuccess ? SWEEP_OK : SWEEP_ECUDA;
+}
+
+int read_error_word(const void *ws, unsigned *bits, cudaStream_t st)
+{
+    unsigned w = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpy(&w, ws, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SWEEP_ECUDA;
+    if (bits) *bits = w;
+    if (w && cudaMemset(const_cast<void *>(ws), 0, sizeof(unsigned)) != cudaSuccess)
+        return SWEEP_ECUDA;
+    return w ? SWEEP_EDEVICE : SWEEP_OK;
+}
+
+// the end of a run: with "check" on, wait for it and read its error word
+int finish_run(const sweep_t *h, int rc, const void *ws, cudaStream_t st)
+{
+    if (rc != SWEEP_OK || !h->check) return rc;
+    return read_error_word(ws, nullptr, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -433,7 +476,7 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     const int k = tile / (2 * n) - 1;  // Eq. 1
     if (depth == 0) depth = k - (k % 2);
     if (depth < 2 || depth > k || (depth % 2) != 0) return SWEEP_EINVAL;
-    sweep_s *h = new (std::nothrow) sweep_s;
+    sweep_s *h = inject(SWEEP_SITE_HOST_ALLOC) ? nullptr : new (std::nothrow) sweep_s;
     if (!h) return SWEEP_ENOMEM;
     h->eqn = eqn;
     h->nx = nx;
@@ -458,6 +501,7 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
                      ? 1 : cluster;
     h->cluster_br = 1;
     h->passes = 1;
+    h->check = 0;
     h->profile = 0;
     h->ev_used = 0;
     // Standard block edge: the first preferred edge that gives at least one
@@ -516,6 +560,9 @@ SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
     } else if (!std::strcmp(key, "passes")) {
         if (v != std::floor(v) || !valid_passes((int)v)) return SWEEP_EINVAL;
         h->passes = (int)v;
+    } else if (!std::strcmp(key, "check")) {
+        if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
+        h->check = (int)v;
     } else if (!std::strcmp(key, "profile")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
         h->profile = (int)v;
@@ -535,6 +582,7 @@ SWEEP_API int sweep_get_param(const sweep_t *h, const char *key, double *v)
     else if (!std::strcmp(key, "scheme")) *v = h->scheme;
     else if (!std::strcmp(key, "standard_tile")) *v = h->std_tile;
     else if (!std::strcmp(key, "profile")) *v = h->profile;
+    else if (!std::strcmp(key, "check")) *v = h->check;
     else if (!std::strcmp(key, "cluster") || !std::strcmp(key, "cluster_oct")) *v = h->cluster;
     else if (!std::strcmp(key, "cluster_bridges")) *v = h->cluster_br;
     else if (!std::strcmp(key, "passes")) *v = h->passes;
@@ -557,17 +605,21 @@ SWEEP_API size_t sweep_workspace_bytes(const sweep_t *h)
 
 SWEEP_API int sweep_run_swept(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws, CUstream_st *stream)
 {
-    const int rc = check_run(h, d_state, nsteps, d_ws);
+    int rc = check_run(h, d_state, nsteps, d_ws);
+    if (rc == SWEEP_OK) rc = clear_error_word(d_ws, stream);
     if (rc != SWEEP_OK) return rc;
-    return run_swept_any(h, make_params(h, d_state, d_ws), nsteps, stream);
+    rc = run_swept_any(h, make_params(h, d_state, d_ws), nsteps, stream);
+    return finish_run(h, rc, d_ws, stream);
 }
 
 SWEEP_API int sweep_run_standard(sweep_t *h, double *d_state, int64_t nsteps, void *d_ws,
                        CUstream_st *stream)
 {
-    const int rc = check_run(h, d_state, nsteps, d_ws);
+    int rc = check_run(h, d_state, nsteps, d_ws);
+    if (rc == SWEEP_OK) rc = clear_error_word(d_ws, stream);
     if (rc != SWEEP_OK) return rc;
-    return run_standard_any(h, make_params(h, d_state, d_ws), nsteps, stream);
+    rc = run_standard_any(h, make_params(h, d_state, d_ws), nsteps, stream);
+    return finish_run(h, rc, d_ws, stream);
 }
 
 SWEEP_API size_t sweep_adjoint_workspace_bytes(const sweep_t *h, int64_t nsteps, int ckpt_every)
@@ -581,6 +633,10 @@ SWEEP_API int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT
 {
     if (!h || !d_lamT || !d_lam0 || !d_ws || nsteps < 0 || ckpt_every < 1) return SWEEP_EINVAL;
     if (!aligned(d_lamT, 16) || !aligned(d_lam0, 16) || !aligned(d_ws, 256)) return SWEEP_EINVAL;
+    if (h->eqn == SWEEP_EULER && (!d_q0 || !aligned(d_q0, 16) || d_lam0 == d_lamT))
+        return SWEEP_EINVAL;
+    int rc = clear_error_word(d_ws, stream);
+    if (rc != SWEEP_OK) return rc;
     if (h->eqn == SWEEP_HEAT) {
         const size_t bytes = sizeof(double) * (size_t)h->nx * (size_t)h->ny;
         if (d_lam0 != d_lamT &&
@@ -589,12 +645,35 @@ SWEEP_API int sweep_adjoint(sweep_t *h, const double *d_q0, const double *d_lamT
         // the heat step is linear with a symmetric stencil: its adjoint step
         // is a stencil update of the same radius, run swept (the
         // forward-Euler step is its own adjoint)
-        if (heat_fe(h)) return swept<HeatFE>(h, make_params(h, d_lam0, d_ws), nsteps, stream);
-        return swept<HeatAdj>(h, make_params(h, d_lam0, d_ws), 2 * nsteps, stream);
+        if (heat_fe(h))
+            rc = swept<HeatFE>(h, make_params(h, d_lam0, d_ws), nsteps, stream);
+        else
+            rc = swept<HeatAdj>(h, make_params(h, d_lam0, d_ws), 2 * nsteps, stream);
+    } else {
+        rc = euler_adjoint(h, d_q0, d_lamT, d_lam0, nsteps, ckpt_every, d_ws, stream);
     }
-    if (!d_q0 || !aligned(d_q0, 16) || d_lam0 == d_lamT) return SWEEP_EINVAL;
-    return euler_adjoint(h, d_q0, d_lamT, d_lam0, nsteps, ckpt_every, d_ws, stream);
+    return finish_run(h, rc, d_ws, stream);
 }
+
+SWEEP_API int sweep_check(const void *d_ws, unsigned *bits, CUstream_st *stream)
+{
+    if (bits) *bits = 0;
+    if (!d_ws || !aligned(d_ws, 256)) return SWEEP_EINVAL;
+    return read_error_word(d_ws, bits, stream);
+}
+
+SWEEP_API int sweep_inject_fault(int site, int nth)
+{
+    if (nth < 0 || (site != 0 && site != SWEEP_SITE_HOST_ALLOC && site != SWEEP_SITE_STREAM_POOL &&
+                    site != SWEEP_SITE_EVENTS))
+        return SWEEP_EINVAL;
+    fault_site.store(0);
+    fault_count.store(nth);
+    if (site != 0 && nth > 0) fault_site.store(site);
+    return SWEEP_OK;
+}
+
+SWEEP_API int sweep_live_cuda_objects(void) { return live_objects.load(); }
 
 // ------------------------------------------------------------------ batch
 //
@@ -627,17 +706,21 @@ int make_batch_pool(BatchPool *bp)
     int ns = 0, ne = 0;
     bool ok = true;
     for (int k = 0; k < kBatchStreams && ok; ++k) {
-        ok = cudaStreamCreateWithFlags(&s[k], cudaStreamNonBlocking) == cudaSuccess;
+        ok = !inject(SWEEP_SITE_STREAM_POOL) &&
+             cudaStreamCreateWithFlags(&s[k], cudaStreamNonBlocking) == cudaSuccess;
         if (ok) ++ns;
-        ok = ok && cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && !inject(SWEEP_SITE_STREAM_POOL) &&
+             cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) == cudaSuccess;
         if (ok) ++ne;
     }
-    ok = ok && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && !inject(SWEEP_SITE_STREAM_POOL) &&
+         cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (int k = 0; k < ne; ++k) cudaEventDestroy(done[k]);
         for (int k = 0; k < ns; ++k) cudaStreamDestroy(s[k]);
         return SWEEP_ECUDA;
     }
+    live_objects += 2 * kBatchStreams + 1;
     for (int k = 0; k < kBatchStreams; ++k) {
         bp->s[k] = s[k];
         bp->done[k] = done[k];
@@ -742,6 +825,7 @@ SWEEP_API void sweep_destroy(sweep_t *h)
 {
     if (!h) return;
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    live_objects -= (int)h->ev.size();
     delete h;
 }
 
@@ -754,6 +838,7 @@ SWEEP_API const char *sweep_error_string(int status)
     case SWEEP_ECUDA: return "CUDA error";
     case SWEEP_ETIMEOUT: return "device wait timed out";
     case SWEEP_EUNSUPPORTED: return "unsupported";
+    case SWEEP_EDEVICE: return "a kernel reported an error (device error word)";
     default: return "unknown status";
     }
 }
@@ -799,7 +884,7 @@ SWEEP_API int sweep_run_swept_static(sweep_t *h, double *d_state, int64_t nsteps
         }
         ws = static_scratch_ptr[dev];
     }
-    return sweep_run_swept(h, d_state, nsteps, ws, stream);
+    return sweep_run_swept(h, d_state, nsteps, ws, stream);  // clears and, with "check", reads the word
 }
 
 }  // extern "C"

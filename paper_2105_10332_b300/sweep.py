@@ -22,6 +22,14 @@ SWEEP_ENOMEM = 2
 SWEEP_ECUDA = 3
 SWEEP_ETIMEOUT = 4
 SWEEP_EUNSUPPORTED = 5
+SWEEP_EDEVICE = 6
+
+SWEEP_DEV_LAUNCH = 1
+SWEEP_DEV_NONFINITE = 2
+
+SWEEP_SITE_HOST_ALLOC = 1
+SWEEP_SITE_STREAM_POOL = 2
+SWEEP_SITE_EVENTS = 3
 
 # every symbol include/sweep.h declares: name -> (restype, argtypes)
 _c_int, _c_i64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -41,6 +49,9 @@ SIGNATURES = {
     "sweep_adjoint": (_c_int, [_vp, _vp, _vp, _vp, _c_i64, _c_int, _vp, _vp]),
     "sweep_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_i64), _c_int]),
     "sweep_fp64_probe": (_c_int, [_vp, _c_i64, _c_int, _c_int, _vp]),
+    "sweep_check": (_c_int, [_vp, ctypes.POINTER(ctypes.c_uint), _vp]),
+    "sweep_inject_fault": (_c_int, [_c_int, _c_int]),
+    "sweep_live_cuda_objects": (_c_int, []),
     "sweep_destroy": (None, [_vp]),
     "sweep_error_string": (ctypes.c_char_p, [_c_int]),
 }
@@ -138,6 +149,21 @@ def sweep_fp64_probe(out_ptr, iters, blocks, threads, stream_ptr):
     return int(lib().sweep_fp64_probe(out_ptr, int(iters), int(blocks), int(threads), stream_ptr))
 
 
+def sweep_check(ws_ptr, stream_ptr):
+    """(status, bits) of the device error word of a workspace (waits for the stream)."""
+    bits = ctypes.c_uint(0)
+    rc = int(lib().sweep_check(ws_ptr, ctypes.byref(bits), stream_ptr))
+    return rc, int(bits.value)
+
+
+def sweep_inject_fault(site, nth):
+    _check(lib().sweep_inject_fault(int(site), int(nth)), "sweep_inject_fault")
+
+
+def sweep_live_cuda_objects():
+    return int(lib().sweep_live_cuda_objects())
+
+
 def sweep_destroy(h):
     lib().sweep_destroy(h)
 
@@ -232,6 +258,19 @@ class Solver:
                            ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream))
         _check(rc, "sweep_adjoint")
         return lam0
+
+    def check(self, ws=None):
+        """Bits of the device error word of this solver's workspace (0: none);
+        waits for the current stream and clears the word."""
+        import torch
+        ws = self._ws if ws is None else ws
+        if ws is None:
+            return 0
+        stream = torch.cuda.current_stream(ws.device).cuda_stream
+        rc, bits = sweep_check(ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream))
+        if rc not in (SWEEP_OK, SWEEP_EDEVICE):
+            _check(rc, "sweep_check")
+        return bits
 
     def profile(self):
         """{kind: (total ms, launches)} of the launches recorded since profiling was enabled."""

@@ -86,6 +86,44 @@ def test_run_rejects_bad_pointers_before_any_launch(L):
     assert S.error_string(S.SWEEP_ETIMEOUT) == "device wait timed out"
 
 
+def test_every_status_has_its_own_message(L):
+    codes = (S.SWEEP_OK, S.SWEEP_EINVAL, S.SWEEP_ENOMEM, S.SWEEP_ECUDA, S.SWEEP_ETIMEOUT,
+             S.SWEEP_EUNSUPPORTED, S.SWEEP_EDEVICE)
+    msgs = [S.error_string(c) for c in codes]
+    assert len(set(msgs)) == len(codes) and "unknown status" not in msgs
+    assert S.error_string(99) == "unknown status"
+
+
+def test_injected_host_allocation_failure(L):
+    """sweep_create's handle allocation, made to fail on the host: SWEEP_ENOMEM,
+    nothing is returned, and the next create succeeds (the fault disarms)."""
+    live = S.sweep_live_cuda_objects()
+    S.sweep_inject_fault(S.SWEEP_SITE_HOST_ALLOC, 2)
+    h1 = S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)  # first pass: fine
+    with pytest.raises(S.SweepError) as e:
+        S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)   # second: fails
+    assert e.value.status == S.SWEEP_ENOMEM
+    h3 = S.sweep_create(S.SWEEP_EULER, 64, 64, 1e-3, 0.1, 32, 6)
+    S.sweep_destroy(h1)
+    S.sweep_destroy(h3)
+    assert S.sweep_live_cuda_objects() == live
+    for site, nth in ((7, 1), (S.SWEEP_SITE_EVENTS, -1)):
+        with pytest.raises(S.SweepError):
+            S.sweep_inject_fault(site, nth)
+    S.sweep_inject_fault(0, 0)
+
+
+def test_check_parameter(L):
+    h = S.sweep_create(S.SWEEP_HEAT, 64, 64, 1e-5, 1 / 64, 16, 6)
+    assert S.sweep_get_param(h, "check") == 0
+    S.sweep_set_param(h, "check", 1)
+    assert S.sweep_get_param(h, "check") == 1
+    with pytest.raises(S.SweepError):
+        S.sweep_set_param(h, "check", 2)
+    S.sweep_destroy(h)
+    assert S.sweep_check(None, None)[0] == S.SWEEP_EINVAL
+
+
 def test_adjoint_workspace_and_argument_checks(L):
     h = S.sweep_create(S.SWEEP_EULER, 64, 64, 1e-3, 0.1, 32, 6)
     slot = (4 * 64 * 64 * 8 + 255) // 256 * 256

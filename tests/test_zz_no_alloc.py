@@ -64,6 +64,15 @@ def test_static_scratch_run_matches_workspace_run(torch_cuda):
             torch.cuda.synchronize()
             assert torch.equal(ua, ub), "heat call %d differs" % call
         assert not torch.equal(a, torch.from_numpy(q0).cuda())
+        # once the library's module is loaded (the calls above), further
+        # calls leave the device's free memory exactly as it was
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            assert S.sweep_run_swept_static(he, _p(b), 7, stream) == S.SWEEP_OK
+            assert S.sweep_run_swept_static(hh, _p(ub), 5, stream) == S.SWEEP_OK
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
     finally:
         S.sweep_destroy(he)
         S.sweep_destroy(hh)
