@@ -406,11 +406,19 @@ __device__ __forceinline__ void copy_unit(double *dst, const double *src, bool t
         *dst = *src;
 }
 
+// Whether a window's shared-memory pairs can be 16-byte aligned: an even
+// origin ox (always, for a block edge that is a multiple of 4) and an even
+// pitch wp (always for the swept windows; a Standard block edge could be
+// odd).  Otherwise every copy takes the one-cell path.
+template <class EQ, int C>
+__device__ __forceinline__ bool pairs_ok(const Block<EQ, C> &B)
+{
+    return ((B.ox | B.wp) & 1) == 0;
+}
+
 // Level-store traffic of one CTA (loads go to this CTA's copy only).  A
 // piece's pairs start on the global column parity of the store's blocks,
-// i.e. window column (ox + shift) mod 2; they are 16-byte aligned in shared
-// memory when the window origin ox is even (always, for a block edge that
-// is a multiple of 4; an odd origin takes the 8-byte path).
+// i.e. window column (ox + shift) mod 2.
 template <class EQ, int C>
 __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &B, int64_t level,
                                                  Rect O, Rect I)
@@ -420,7 +428,7 @@ __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     const int par = (int)((B.ox + shift) & 1);
-    for_units(O, I, par, (B.ox & 1) == 0, [&](int x, int y, bool two) {
+    for_units(O, I, par, pairs_ok(B), [&](int x, int y, bool two) {
         const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c) {
@@ -442,7 +450,7 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     const int par = (int)((B.ox + shift) & 1);
-    for_units(O, I, par, (B.ox & 1) == 0, [&](int x, int y, bool two) {
+    for_units(O, I, par, pairs_ok(B), [&](int x, int y, bool two) {
         const int64_t g = sidx(p, B.ox, B.oy, x, y, shift);
 #pragma unroll
         for (int c = 0; c < EQ::NC; ++c)
@@ -452,9 +460,9 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
 
 // A whole rectangle R of the window between the row-major state (global,
 // periodic) and buffer `buf` of shared memory, in 16-byte pairs of cells
-// (x, x+1), x even, where the window origin is even and the buffer has no
-// one-double offset (a pair never straddles the periodic seam: nx is even);
-// one cell at a time otherwise.  to_smem: state -> shared memory, else
+// (x, x+1), x even, where pairs_ok holds and the buffer has no one-double
+// offset (a pair never straddles the periodic seam: nx is even); one cell at
+// a time otherwise.  to_smem: state -> shared memory, else
 // shared memory -> state.
 template <class EQ, int C>
 __device__ __forceinline__ void state_rect(const Params &p, Block<EQ, C> &B, double *state, int buf,
@@ -462,7 +470,7 @@ __device__ __forceinline__ void state_rect(const Params &p, Block<EQ, C> &B, dou
 {
     const int64_t gplane = p.nx * p.ny;
     double *sm = B.buf[buf];
-    const bool vec = (B.ox & 1) == 0 && (buf == 0 || Block<EQ, C>::kHoff == 0);
+    const bool vec = pairs_ok(B) && (buf == 0 || Block<EQ, C>::kHoff == 0);
     bool bad = false;
     for_units(R, Rect{0, 0, 0, 0}, 0, vec, [&](int x, int y, bool two) {
         const int64_t g = gidx(p, B.ox, B.oy, x, y);
