@@ -14,6 +14,8 @@ carries the Euler vortex at 256 x 256 advanced to t = 10 (2999 steps, block
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload heat16384|euler256|euler1024|heat64|heat4096|adjoint1024|batch256]
   python bench.py --peaks                      # the FP64 probe alone
+  python bench.py --workload heat16384|heat64|euler256 --sweep
+        # the block-size sweep (tile edge x depth x cluster), one line each
   python bench.py --workload W --ncu-run swept|standard
         # W warm-up runs then one run, nothing timed: the command that the
         # ncu captures summarised under profiles/ run
@@ -602,6 +604,78 @@ def run_ncu(args, wl):
                       "launches_per_run": {k: v[1] for k, v in prof.items()}}), flush=True)
 
 
+SWEEP_PLANS = {
+    # the block-size sweep of the large heat workload: tile edges 8-64, for each
+    # the largest even depth and about half of it (edges 12 and 24 do not
+    # divide 16384 and run on 16368 = 12 x 1364 = 24 x 682)
+    "heat16384": dict(tiles=(8, 12, 16, 24, 32, 48, 64), clusters=(1,), depths="max_half"),
+    # the small heat grid: every depth and cluster size of edges 8, 16, 32
+    "heat64": dict(tiles=(8, 16, 32), clusters=(1, 2, 4), depths="all"),
+    "euler256": dict(tiles=(16, 32), clusters=(1, 2, 4), depths="all"),
+}
+
+
+def sweep_configs(wl, plan):
+    """(nx, tile, depth, cluster) of a block-size sweep of workload wl."""
+    n = 1 if wl["eqn"] == "heat" else 2
+    out = []
+    for b in plan["tiles"]:
+        nx = (wl["nx"] // b) * b  # the largest multiple of the edge that fits
+        if nx // b < 2 or nx % 2:
+            continue
+        k = b // (2 * n) - 1
+        ds = [d for d in range(2, k + 1, 2)]
+        if not ds:
+            continue
+        if plan["depths"] == "max_half":
+            ds = sorted({ds[-1], ds[max(0, len(ds) // 2 - 1)]})
+        for d in ds:
+            for c in plan["clusters"]:
+                out.append((nx, b, d, c))
+    return out
+
+
+def run_sweep(args, wl):
+    """Swept Gcell-steps/s of the workload for each (tile, depth, cluster) of
+    its plan, and Standard once per grid size; one JSON line per
+    configuration (graph replay, L2 flushed, K = --steps runs each)."""
+    import torch
+    from paper_2105_10332_b300 import sweep as S, workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = SWEEP_PLANS[args.workload]
+    done_std, states = set(), {}
+    for nx, b, d, c in sweep_configs(wl, plan):
+        cfg = dict(wl)
+        if nx != wl["nx"]:  # heat only: the edge does not divide the grid
+            if nx not in states:
+                states[nx] = W.heat_modes(nx, nx)
+            cfg.update(nx=nx, ny=nx, name=wl["name"].replace(str(wl["nx"]), str(nx)),
+                       state=states[nx])
+            cfg["dt"], cfg["dx"] = W.heat_dt(nx, 0.1)
+        cfg.update(tile=b, depth=d)
+        try:
+            r = Runner(cfg, dev)
+            if c != r.solver.get("cluster_oct") or c != r.solver.get("cluster_bridges"):
+                r.solver.set("cluster", c)
+        except S.SweepError as e:
+            print(json.dumps({"sweep": cfg["name"], "tile": b, "depth": d, "cluster": c,
+                              "skipped": str(e)}), flush=True)
+            continue
+        r.warm("run_swept", 1)
+        ms = r.timed("run_swept", args.steps) / args.steps
+        line = {"sweep": cfg["name"], "tile": b, "depth": d, "cluster": c,
+                "swept": round(job_rate(1, r.cells, r.N, 1, ms / 1e3), 4), "ms_per_run": round(ms, 4)}
+        if nx not in done_std:
+            r.warm("run_standard", 1)
+            mt = r.timed("run_standard", args.steps) / args.steps
+            line.update(standard=round(job_rate(1, r.cells, r.N, 1, mt / 1e3), 4),
+                        standard_tile=int(r.solver.get("standard_tile")))
+            done_std.add(nx)
+        print(json.dumps(line), flush=True)
+        del r
+        torch.cuda.empty_cache()
+
+
 def run_ours(args, wl):
     import torch
     world, rank, local = dist_setup()
@@ -725,6 +799,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--ncu-run", choices=["swept", "standard"], default=None)
+    ap.add_argument("--sweep", action="store_true")
     args = ap.parse_args()
     if args.peaks:
         run_peaks(args)
@@ -736,6 +811,8 @@ def main():
         run_reference(args, wl)
     elif args.ncu_run:
         run_ncu(args, wl)
+    elif args.sweep:
+        run_sweep(args, wl)
     elif wl.get("adjoint"):
         run_adjoint(args, wl)
     elif wl.get("batch"):

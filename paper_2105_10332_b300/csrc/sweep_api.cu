@@ -521,6 +521,10 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
             h->std_tile = t;
         }
     }
+    // no preferred edge divides the grid (e.g. 56 x 84): the even edge in
+    // [8, 64] that gives the most blocks
+    for (int t = 8; h->std_tile == 0 && t <= 64; t += 2)
+        if (valid_std_tile(h, t)) h->std_tile = t;
     if (h->std_tile == 0) {
         delete h;
         return SWEEP_EINVAL;

@@ -220,6 +220,10 @@ def test_standard_tile_default_fills_the_sms(L):
         h = S.sweep_create(eqn, nx, nx, 1e-6, 1.0 / nx, tile, 0)
         assert S.sweep_get_param(h, "standard_tile") == expect, (eqn, nx)
         S.sweep_destroy(h)
+    # no edge of the preferred list divides 56 x 84: the smallest even one that does
+    h = S.sweep_create(S.SWEEP_HEAT, 56, 84, 1e-6, 1.0 / 56, 14, 0)
+    assert S.sweep_get_param(h, "standard_tile") == 14
+    S.sweep_destroy(h)
 
 
 
