@@ -44,11 +44,12 @@ struct HeatAdj {
 
 template <int C>
 struct Stage<HeatAdj, C> {
-    __device__ static void run(const Params &p, Block<HeatAdj, C> &B, int64_t level, Rect R)
+    __device__ __forceinline__ static void run(const Params &p, Block<HeatAdj, C> &B, int64_t level,
+                                               Rect R)
     {
         const bool second = (level & 1) == 0;
-        const double *src = B.buf[(level - 1) & 1];
-        const double *own = B.buf[level & 1];
+        const double *src = B.lev(level - 1);
+        const double *own = B.lev(level);
         const int wp = B.wp;
         const Fx F = p.ek.f;
         for_rect(band(R, B.rank, C), [&](int x, int y) {
@@ -243,7 +244,7 @@ __device__ __forceinline__ void face_flux_vjp(const double q1[4], const double q
 
 // Per cell: cp[0..3][cell] = pressure, 1/rho, u, v (the arithmetic of
 // cell_pressure, whose sum of momentum terms is symmetric in x and y).
-__global__ void __launch_bounds__(kThreads) k_vjp_cells(Params p, const double *q, double *cp)
+__global__ void __launch_bounds__(kThreads) k_vjp_cells(const __grid_constant__ Params p, const double *q, double *cp)
 {
     const int64_t plane = p.nx * p.ny;
     const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_cells(Params p, const double *
 // Per cell and axis: lp[(axis*6 + t)*plane + cell] = h+, dh+/ddm, dh+/ddp,
 // h-, dh-/ddm, dh-/ddp of the cell's half limiter factors, from
 // dm = P_i - P_{i-1} and dp = P_{i+1} - P_i along the axis.
-__global__ void __launch_bounds__(kThreads) k_vjp_limiters(Params p, const double *cp, double *lp)
+__global__ void __launch_bounds__(kThreads) k_vjp_limiters(const __grid_constant__ Params p, const double *cp, double *lp)
 {
     const int64_t plane = p.nx * p.ny;
     const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_limiters(Params p, const doubl
 constexpr int kVjpThreads = SWEEP_VJP_THREADS;
 constexpr int kFacePlanes = 12;  // per axis
 __global__ void __launch_bounds__(kVjpThreads, 512 / kVjpThreads)
-    k_face_vjp(Params p, const double *q, const double *lp, const double *v, double *fo)
+    k_face_vjp(const __grid_constant__ Params p, const double *q, const double *lp, const double *v, double *fo)
 {
     const int64_t plane = p.nx * p.ny;
     const Fx F = p.ek.f;
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(kVjpThreads, 512 / kVjpThreads)
 // pb (q, cp: the state and its k_vjp_cells terms), and
 //   mode 0:  mu = lam2 S                 (mu: out)
 //   mode 1:  lam = (lam + mu) + lam1 S   (lam: in place)
-__global__ void __launch_bounds__(kThreads) k_gather(Params p, const double *fo, const double *q,
+__global__ void __launch_bounds__(kThreads) k_gather(const __grid_constant__ Params p, const double *fo, const double *q,
                                                      const double *cp, double *lam, double *mu,
                                                      int mode)
 {

@@ -106,6 +106,8 @@ struct Params {
     // Device error word (the first 4 bytes of the workspace header), or null:
     // kernels OR in the kErr* bits below; the host reads it with sweep_check.
     unsigned *err;
+    int check_out;  // this launch writes a run's final state: check it for infinities and NaNs
+    int narrow;     // nx * ny < 2^31: cell and block indices of a plane fit in 32 bits
 };
 
 // Bits of the device error word.
@@ -224,6 +226,31 @@ struct Block {
 
     int bands;       // row bands per level: C x passes
 
+    // Level l lives in slot l mod (d+1) of the level store.  The kernel's
+    // first level and its slot are set once (set_levels); every later level
+    // of the launch, at most 2d above it, finds its slot by subtraction
+    // instead of a 64-bit division per access.
+    int64_t lbase;
+    int sbase;
+    __device__ void set_levels(const Params &p, int64_t base)
+    {
+        lbase = base;
+        sbase = (int)(base % (p.d + 1));
+    }
+    __device__ __forceinline__ double *slot(const Params &p, int64_t level) const
+    {
+        const int d1 = p.d + 1;
+        int sl = (int)(level - lbase) + sbase;
+        if (sl >= d1) sl -= d1;
+        if (sl >= d1) sl -= d1;
+        return p.ws + (int64_t)sl * p.slot_elems;
+    }
+
+    // buffer of a level (F for even levels, H for odd).  A select on the
+    // parity, not an index into buf[]: an array indexed at run time would
+    // live in local memory, and so would every field of the block.
+    __device__ __forceinline__ double *lev(int64_t level) const { return (level & 1) ? buf[1] : buf[0]; }
+
     __device__ void carve(double *smem, int wp_, int passes = 1)
     {
         bands = C * passes;
@@ -281,6 +308,15 @@ __device__ __forceinline__ void level_barrier()
 
 __device__ __forceinline__ int64_t gidx(const Params &p, int64_t ox, int64_t oy, int x, int y)
 {
+    if (p.narrow) {  // the same arithmetic in 32 bits
+        const int nx = (int)p.nx, ny = (int)p.ny;
+        int gx = (int)ox + x, gy = (int)oy + y;
+        if (gx < 0) gx += nx;
+        if (gx >= nx) gx -= nx;
+        if (gy < 0) gy += ny;
+        if (gy >= ny) gy -= ny;
+        return (int64_t)(gy * nx + gx);
+    }
     int64_t gx = ox + x, gy = oy + y;
     // windows start inside [0, n) and extend at most one grid period
     if (gx < 0) gx += p.nx;
@@ -352,10 +388,6 @@ __device__ __forceinline__ void for_rect(Rect R, F &&f)
         f(R.x0 + q % w, R.y0 + q / w);
 }
 
-__device__ __forceinline__ double *slot_ptr(const Params &p, int64_t level)
-{
-    return p.ws + (level % (p.d + 1)) * p.slot_elems;
-}
 
 // Index of the window cell (x, y) of the window at (ox, oy) inside one
 // component plane of a level-store slot.  The store keeps each 2 x 2 block
@@ -370,6 +402,15 @@ __device__ __forceinline__ double *slot_ptr(const Params &p, int64_t level)
 __device__ __forceinline__ int64_t sidx(const Params &p, int64_t ox, int64_t oy, int x, int y,
                                         int shift)
 {
+    if (p.narrow) {  // the same arithmetic in 32 bits
+        const int nx = (int)p.nx, ny = (int)p.ny;
+        int gx = (int)ox + x + shift, gy = (int)oy + y + shift;
+        if (gx < 0) gx += nx;
+        if (gx >= nx) gx -= nx;
+        if (gy < 0) gy += ny;
+        if (gy >= ny) gy -= ny;
+        return (int64_t)((((gy >> 1) * (nx >> 1) + (gx >> 1)) << 2) + ((gy & 1) << 1) + (gx & 1));
+    }
     int64_t gx = ox + x + shift, gy = oy + y + shift;
     if (gx < 0) gx += p.nx;
     if (gx >= p.nx) gx -= p.nx;
@@ -423,8 +464,8 @@ template <class EQ, int C>
 __device__ __forceinline__ void load_level_async(const Params &p, Block<EQ, C> &B, int64_t level,
                                                  Rect O, Rect I)
 {
-    const double *src = slot_ptr(p, level);
-    double *dst = B.buf[level & 1];
+    const double *src = B.slot(p, level);
+    double *dst = B.lev(level);
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     const int par = (int)((B.ox + shift) & 1);
@@ -445,8 +486,8 @@ template <class EQ, int C>
 __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, int64_t level, Rect O,
                                             Rect I)
 {
-    double *dst = slot_ptr(p, level);
-    const double *src = B.buf[level & 1];
+    double *dst = B.slot(p, level);
+    const double *src = B.lev(level);
     const int64_t gplane = p.nx * p.ny;
     const int shift = EQ::N == 1 ? (int)(level & 1) : 0;
     const int par = (int)((B.ox + shift) & 1);
@@ -462,14 +503,16 @@ __device__ __forceinline__ void store_level(const Params &p, Block<EQ, C> &B, in
 // periodic) and buffer `buf` of shared memory, in 16-byte pairs of cells
 // (x, x+1), x even, where pairs_ok holds and the buffer has no one-double
 // offset (a pair never straddles the periodic seam: nx is even); one cell at
-// a time otherwise.  to_smem: state -> shared memory, else
-// shared memory -> state.
+// a time otherwise.  to_smem: state -> shared memory, else shared memory ->
+// state, where `check` (set for the launch that writes a run's final state:
+// an infinity or a NaN anywhere in a run reaches it) reports non-finite
+// values in the device error word.
 template <class EQ, int C>
 __device__ __forceinline__ void state_rect(const Params &p, Block<EQ, C> &B, double *state, int buf,
-                                           Rect R, bool to_smem)
+                                           Rect R, bool to_smem, bool check = false)
 {
     const int64_t gplane = p.nx * p.ny;
-    double *sm = B.buf[buf];
+    double *sm = buf ? B.buf[1] : B.buf[0];
     const bool vec = pairs_ok(B) && (buf == 0 || Block<EQ, C>::kHoff == 0);
     bool bad = false;
     for_units(R, Rect{0, 0, 0, 0}, 0, vec, [&](int x, int y, bool two) {
@@ -482,7 +525,8 @@ __device__ __forceinline__ void state_rect(const Params &p, Block<EQ, C> &B, dou
                 copy_unit(s, d, two);
             } else {
                 copy_unit(d, s, two);
-                bad = bad || nonfinite(s[0]) || (two && nonfinite(s[1]));
+                if (check)
+                    bad = bad || nonfinite(s[0]) || (two && nonfinite(s[1]));
             }
         }
     });
@@ -502,11 +546,12 @@ struct Stage;
 
 template <int C>
 struct Stage<Heat, C> {
-    __device__ static void run(const Params &p, Block<Heat, C> &B, int64_t level, Rect R)
+    __device__ __forceinline__ static void run(const Params &p, Block<Heat, C> &B, int64_t level,
+                                               Rect R)
     {
         const bool second = (level & 1) == 0;
-        const double *src = B.buf[(level - 1) & 1];
-        const double *own = second ? B.buf[level & 1] : src;
+        const double *src = B.lev(level - 1);
+        const double *own = second ? B.lev(level) : src;
         const double c = second ? p.c2 : p.c1;
         const int wp = B.wp;
         for_rect(band(R, B.rank, C), [&](int x, int y) {
@@ -520,9 +565,10 @@ struct Stage<Heat, C> {
 
 template <int C>
 struct Stage<HeatFE, C> {
-    __device__ static void run(const Params &p, Block<HeatFE, C> &B, int64_t level, Rect R)
+    __device__ __forceinline__ static void run(const Params &p, Block<HeatFE, C> &B, int64_t level,
+                                               Rect R)
     {
-        const double *src = B.buf[(level - 1) & 1];
+        const double *src = B.lev(level - 1);
         const int wp = B.wp;
         for_rect(band(R, B.rank, C), [&](int x, int y) {
             const int i = y * wp + x;
@@ -539,7 +585,8 @@ struct Stage<HeatFE, C> {
 // the level history of Params.
 template <class EQ, int C, bool HIST>
 struct EulerStage {
-    __device__ static void run(const Params &p, Block<EQ, C> &B, int64_t level, Rect R)
+    __device__ __forceinline__ static void run(const Params &p, Block<EQ, C> &B, int64_t level,
+                                               Rect R)
     {
         const int np = B.bands / C;
         for (int k = 0; k < np; ++k) {
@@ -547,11 +594,12 @@ struct EulerStage {
             run_band(p, B, level, band(R, B.rank * np + k, B.bands));
         }
     }
-    __device__ static void run_band(const Params &p, Block<EQ, C> &B, int64_t level, Rect S)
+    __device__ __forceinline__ static void run_band(const Params &p, Block<EQ, C> &B, int64_t level,
+                                                    Rect S)
     {
         const bool second = (level & 1) == 0;
-        const double *src = B.buf[(level - 1) & 1];
-        const double *own = second ? B.buf[level & 1] : src;
+        const double *src = B.lev(level - 1);
+        const double *own = second ? B.lev(level) : src;
         const double lam = second ? p.c2 : p.c1;
         const int wp = B.wp, pl = B.plane;
         const EulerConst k = p.ek;
@@ -812,7 +860,8 @@ __device__ __forceinline__ void export_band(const Params &p, Block<EQ, C> &B, in
 // sits where a level computed before its use is written (the rings of one
 // parity grow outwards, the computed regions stay inside them).
 template <class EQ, int C>
-__device__ void preload_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base, bool top)
+__device__ __forceinline__ void preload_growing(const Params &p, Block<EQ, C> &B, int kind,
+                                                int64_t base, bool top)
 {
     const int n = EQ::N, b = p.b, d = p.d;
     Rect prev = {0, 0, 0, 0};
@@ -829,7 +878,7 @@ __device__ void preload_growing(const Params &p, Block<EQ, C> &B, int kind, int6
 
 // A shape that grows from nothing, its inputs already preloaded.
 template <class EQ, int C>
-__device__ void run_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base)
+__device__ __forceinline__ void run_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base)
 {
     const int n = EQ::N, b = p.b, d = p.d;
     for (int s = 1; s <= d; ++s) {
@@ -845,7 +894,7 @@ __device__ void run_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t 
 // An Up-Pyramid on the window whose level `base` is already in buffer F of
 // every CTA of the cluster.
 template <class EQ, int C>
-__device__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
+__device__ __forceinline__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 {
     const int n = EQ::N, b = p.b, d = p.d;
     export_band(p, B, kUp, 0, base, shape_rect(kUp, b, n, 0));
@@ -863,7 +912,7 @@ __device__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 
 // Up-Pyramid on block (I, J) of the unshifted grid; level 0 is the state.
 template <class EQ, int C>
-__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_up(const __grid_constant__ Params p)
 {
     extern __shared__ __align__(16) double smem[];
     const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
@@ -875,6 +924,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
     const int I = t % p.tiles_x, J = t / p.tiles_x;
     B.ox = (int64_t)I * p.b;
     B.oy = (int64_t)J * p.b;
+    B.set_levels(p, 0);
     state_rect(p, B, p.state, 0, Rect{0, p.b, 0, p.b}, true);
     level_barrier<C>();  // also: every CTA of the cluster has started
     run_pyramid<EQ, C>(p, B, 0);
@@ -884,7 +934,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_up(Params p)
 // X- and Y-Bridges on the seams of the grid with offset o; shape 2t is the
 // X-Bridge right of block t, shape 2t+1 the Y-Bridge above it.
 template <class EQ, int C>
-__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t base, int o)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_bridges(const __grid_constant__ Params p, int64_t base, int o)
 {
     extern __shared__ __align__(16) double smem[];
     const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
@@ -900,6 +950,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t
     B.oy = (int64_t)J * p.b + o + (kind == kYBridge ? h : 0);
     if (B.ox >= p.nx) B.ox -= p.nx;
     if (B.oy >= p.ny) B.oy -= p.ny;
+    B.set_levels(p, base);
     preload_growing<EQ, C>(p, B, kind, base, false);
     if constexpr (C > 1) cg::this_cluster().sync();
     run_growing<EQ, C>(p, B, kind, base);
@@ -911,7 +962,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_bridges(Params p, int64_t
 // last != 0 makes it the Down-Pyramid: the lower half only, after which the
 // window, now complete at level base+d, is written to the state.
 template <class EQ, int C>
-__global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int64_t base, int o, int last)
+__global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_octahedron(const __grid_constant__ Params p, int64_t base, int o, int last)
 {
     extern __shared__ __align__(16) double smem[];
     const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
@@ -926,6 +977,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int6
     B.oy = (int64_t)J * p.b + o + h;
     if (B.ox >= p.nx) B.ox -= p.nx;
     if (B.oy >= p.ny) B.oy -= p.ny;
+    B.set_levels(p, base);
     preload_growing<EQ, C>(p, B, kLower, base, true);
     if constexpr (C > 1) cg::this_cluster().sync();
     run_growing<EQ, C>(p, B, kLower, base);
@@ -934,7 +986,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int6
     if (!last) {
         run_pyramid<EQ, C>(p, B, top);
     } else {
-        state_rect(p, B, p.state, (int)(top & 1), band(whole, B.rank, C), false);
+        state_rect(p, B, p.state, (int)(top & 1), band(whole, B.rank, C), false, true);
     }
     if constexpr (C > 1) cg::this_cluster().sync();
 }
@@ -944,7 +996,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS) k_octahedron(Params p, int6
 // and stage 2 on the tile, and writes the tile to dst (and, if qstar is
 // not null, the tile's first-stage values to qstar).
 template <class EQ>
-__global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(Params p, const double *src, double *dst,
+__global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(const __grid_constant__ Params p, const double *src, double *dst,
                                                        double *qstar)
 {
     extern __shared__ __align__(16) double smem[];
@@ -966,13 +1018,13 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(Params p, const do
         state_rect(p, B, qstar, 1, tile, false);
     Stage<EQ, 1>::run(p, B, 2, tile);
     __syncthreads();
-    state_rect(p, B, dst, 0, tile, false);
+    state_rect(p, B, dst, 0, tile, false, p.check_out != 0);
 }
 
 // One level on every cell (tiles of std_tile with a halo of n): the first
 // RK2 stage (rebuilt for the adjoint), or one forward-Euler step.
 template <class EQ>
-__global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(Params p, const double *src, double *dst)
+__global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(const __grid_constant__ Params p, const double *src, double *dst)
 {
     extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 2 * n;
@@ -988,7 +1040,7 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(Params p, const doub
     __syncthreads();
     Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
-    state_rect(p, B, dst, 1, Rect{n, wp - n, n, wp - n}, false);
+    state_rect(p, B, dst, 1, Rect{n, wp - n, n, wp - n}, false, p.check_out != 0);
 }
 
 }  // namespace sweep

@@ -121,6 +121,8 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     p.hist_stride = 0;
     p.hist_levels = 0;
     p.err = ws ? (unsigned *)ws : nullptr;
+    p.check_out = 0;
+    p.narrow = h->nx * h->ny < (int64_t(1) << 31) ? 1 : 0;
     return p;
 }
 
@@ -180,10 +182,15 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
         return SWEEP_ECUDA;
     const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
     double *a = p.state, *b = p.ws;
+    // the launch that writes the run's final state checks it for infinities
+    // and NaNs (device error word)
+    Params last = p;
+    last.check_out = 1;
     for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
-            k_standard<EQ><<<grid, EQ::STD_THREADS, smem, st>>>(p, a, b, nullptr);
+            k_standard<EQ><<<grid, EQ::STD_THREADS, smem, st>>>(l + 2 >= nlevels ? last : p, a, b,
+                                                              nullptr);
         }
         double *t = a;
         a = b;
@@ -192,7 +199,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     if (nlevels & 1) {
         {
             Bracket br(h, st, kKindStandard);
-            k_level1<EQ><<<grid, EQ::STD_THREADS, smem1, st>>>(p, a, b);
+            k_level1<EQ><<<grid, EQ::STD_THREADS, smem1, st>>>(last, a, b);
         }
         double *t = a;
         a = b;
