@@ -120,6 +120,17 @@ int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile
  *   "profile"        1: every later run brackets each kernel launch with a
  *                    pair of CUDA events on its stream (read them with
  *                    sweep_profile_read); 0 (default): no events
+ *   "l2_fetch_bytes" 32, 64 or 128: set, at once, the L2 fetch granularity
+ *                    limit (cudaLimitMaxL2FetchGranularity) of the calling
+ *                    process's CUDA context on the current device -- it
+ *                    applies to every kernel of the process until changed,
+ *                    and ends with the process.  The level store's thin
+ *                    column pieces use one 32-byte sector of each 128-byte
+ *                    line; with 32 the swept kernels' DRAM reads drop to the
+ *                    bytes they use (heat, block 64, depth 30: 2.5x -> 1.0x
+ *                    per launch; run time unchanged, the kernels being bound
+ *                    by FP64 issue).  0 (default): the context is not touched.
+ *                    Returns SWEEP_ECUDA if the limit cannot be set.
  *   "check"          1: every run (swept, standard, adjoint, static) ends
  *                    by waiting for its stream and reading the device error
  *                    word, and returns SWEEP_EDEVICE if a bit is set (the

@@ -106,6 +106,7 @@ struct Params {
     // Device error word (the first 4 bytes of the workspace header), or null:
     // kernels OR in the kErr* bits below; the host reads it with sweep_check.
     unsigned *err;
+    int std_tx, std_blocks;  // Standard blocks along x, and in all (nx/std_tile, that x ny/std_tile)
     int check_out;  // this launch writes a run's final state: check it for infinities and NaNs
     int narrow;     // nx * ny < 2^31: cell and block indices of a plane fit in 32 bits
 };
@@ -326,24 +327,38 @@ __device__ __forceinline__ int64_t gidx(const Params &p, int64_t ox, int64_t oy,
     return gy * p.nx + gx;
 }
 
-// Visit O \ I (I inside O or empty) with the CTA's threads, packed linearly
-// so that no lane idles while work is left, in units: where a part of O \ I
-// starts on a window column x = par (mod 2) and is an even number of cells
-// wide, and vec is set, a unit is the pair of cells (x, x+1) (f gets
-// two = true); elsewhere a unit is one cell.  O \ I is taken as the parts
-// below I, above I (full width), left of I and right of I.
+// Visit one rectangle R with the CTA's threads in units: the pair of cells
+// (x, x+1) when `vec` is set and R starts on a window column x = par (mod 2)
+// and is an even number of cells wide (f gets two = true), else one cell.
+template <class F>
+__device__ __forceinline__ void for_rect_units(Rect R, int par, bool vec, F &&f)
+{
+    const int w = R.w(), h = R.h();
+    if (w == 0 || h == 0)
+        return;
+    const bool two = vec && ((R.x0 - par) & 1) == 0 && (w & 1) == 0;
+    const int wu = two ? w >> 1 : w, step = two ? 2 : 1;
+    const int total = wu * h;
+    for (int q = threadIdx.x; q < total; q += blockDim.x)
+        f(R.x0 + (q % wu) * step, R.y0 + q / wu, two);
+}
+
+// Visit O \ I (I inside O or empty) in the units of for_rect_units, the
+// parts below I, above I (full width), left of I and right of I packed into
+// one index space, so that no lane idles while work is left and the whole
+// of O \ I costs one loop (these copies lie on the critical path of small
+// shapes, where one loop per part would cost four loops' latency).
 template <class F>
 __device__ __forceinline__ void for_units(Rect O, Rect I, int par, bool vec, F &&f)
 {
     if (O.empty())
         return;
-    Rect a = O, b = {0, 0, 0, 0}, c = {0, 0, 0, 0}, e = {0, 0, 0, 0};
-    if (!I.empty()) {
-        a = {O.x0, O.x1, O.y0, I.y0};
-        b = {O.x0, O.x1, I.y1, O.y1};
-        c = {O.x0, I.x0, I.y0, I.y1};
-        e = {I.x1, O.x1, I.y0, I.y1};
+    if (I.empty()) {
+        for_rect_units(O, par, vec, f);
+        return;
     }
+    const Rect a = {O.x0, O.x1, O.y0, I.y0}, b = {O.x0, O.x1, I.y1, O.y1};
+    const Rect c = {O.x0, I.x0, I.y0, I.y1}, e = {I.x1, O.x1, I.y0, I.y1};
     auto pairs = [&](const Rect &R) {
         return vec && !R.empty() && ((R.x0 - par) & 1) == 0 && (R.w() & 1) == 0;
     };
@@ -1001,12 +1016,11 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(const __grid_const
 {
     extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 4 * n;
-    if (!launch_ok(p, (unsigned)((p.nx / T) * (p.ny / T)), EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
+    if (!launch_ok(p, (unsigned)p.std_blocks, EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
         return;
     Block<EQ, 1> B;
     B.carve(smem, wp);
-    const int tx = (int)(p.nx / T);
-    const int I = blockIdx.x % tx, J = blockIdx.x / tx;
+    const int I = blockIdx.x % p.std_tx, J = blockIdx.x / p.std_tx;
     B.ox = (int64_t)I * T - 2 * n;
     B.oy = (int64_t)J * T - 2 * n;
     state_rect(p, B, const_cast<double *>(src), 0, Rect{0, wp, 0, wp}, true);
@@ -1028,12 +1042,11 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_level1(const __grid_constan
 {
     extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 2 * n;
-    if (!launch_ok(p, (unsigned)((p.nx / T) * (p.ny / T)), EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
+    if (!launch_ok(p, (unsigned)p.std_blocks, EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
         return;
     Block<EQ, 1> B;
     B.carve(smem, wp);
-    const int tx = (int)(p.nx / T);
-    const int I = blockIdx.x % tx, J = blockIdx.x / tx;
+    const int I = blockIdx.x % p.std_tx, J = blockIdx.x / p.std_tx;
     B.ox = (int64_t)I * T - n;
     B.oy = (int64_t)J * T - n;
     state_rect(p, B, const_cast<double *>(src), 0, Rect{0, wp, 0, wp}, true);

@@ -29,6 +29,7 @@ struct sweep_s {
     int cluster_br;  // CTAs per Bridge window (1, 2 or 4)
     int passes;      // sub-bands per CTA and level (1, 2 or 4)
     int check;       // 1: every run ends by reading the device error word (synchronous)
+    int l2_fetch;    // L2 fetch granularity this handle set for the context (0: untouched)
     // optional per-launch event timing ("profile" parameter)
     int profile;
     std::vector<cudaEvent_t> ev;   // start/end pairs, reused across runs
@@ -98,6 +99,8 @@ Params make_params(const sweep_s *h, double *state, void *ws)
     p.tiles_x = (int)(h->nx / h->tile);
     p.tiles_y = (int)(h->ny / h->tile);
     p.std_tile = h->std_tile;
+    p.std_tx = (int)(h->nx / h->std_tile);
+    p.std_blocks = p.std_tx * (int)(h->ny / h->std_tile);
     if (h->eqn == SWEEP_HEAT) {
         const double r = (h->alpha * h->dt) / (h->dx * h->dx);
         p.c1 = 0.5 * r;
@@ -509,6 +512,7 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->cluster_br = 1;
     h->passes = 1;
     h->check = 0;
+    h->l2_fetch = 0;
     h->profile = 0;
     h->ev_used = 0;
     // Standard block edge: the first preferred edge that gives at least one
@@ -574,6 +578,12 @@ SWEEP_API int sweep_set_param(sweep_t *h, const char *key, double v)
     } else if (!std::strcmp(key, "check")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
         h->check = (int)v;
+    } else if (!std::strcmp(key, "l2_fetch_bytes")) {
+        if (v != 0.0 && v != 32.0 && v != 64.0 && v != 128.0) return SWEEP_EINVAL;
+        if (v != 0.0 &&
+            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)v) != cudaSuccess)
+            return SWEEP_ECUDA;
+        h->l2_fetch = (int)v;
     } else if (!std::strcmp(key, "profile")) {
         if (v != 0.0 && v != 1.0) return SWEEP_EINVAL;
         h->profile = (int)v;
@@ -594,6 +604,7 @@ SWEEP_API int sweep_get_param(const sweep_t *h, const char *key, double *v)
     else if (!std::strcmp(key, "standard_tile")) *v = h->std_tile;
     else if (!std::strcmp(key, "profile")) *v = h->profile;
     else if (!std::strcmp(key, "check")) *v = h->check;
+    else if (!std::strcmp(key, "l2_fetch_bytes")) *v = h->l2_fetch;
     else if (!std::strcmp(key, "cluster") || !std::strcmp(key, "cluster_oct")) *v = h->cluster;
     else if (!std::strcmp(key, "cluster_bridges")) *v = h->cluster_br;
     else if (!std::strcmp(key, "passes")) *v = h->passes;

@@ -120,6 +120,12 @@ def test_check_parameter(L):
     assert S.sweep_get_param(h, "check") == 1
     with pytest.raises(S.SweepError):
         S.sweep_set_param(h, "check", 2)
+    for bad in (16, 48, 256, -32):
+        with pytest.raises(S.SweepError) as e:
+            S.sweep_set_param(h, "l2_fetch_bytes", bad)
+        assert e.value.status == S.SWEEP_EINVAL
+    S.sweep_set_param(h, "l2_fetch_bytes", 0)  # 0 leaves the context untouched: no CUDA call
+    assert S.sweep_get_param(h, "l2_fetch_bytes") == 0
     S.sweep_destroy(h)
     assert S.sweep_check(None, None)[0] == S.SWEEP_EINVAL
 

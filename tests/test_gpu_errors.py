@@ -6,7 +6,8 @@ write the state set SWEEP_DEV_NONFINITE, which sweep_check (or a run with
 The batch stream pool: a stream or event creation made to fail on the host
 returns SWEEP_ECUDA and leaves nothing behind, and the next call builds the
 pool and runs.  The launch-geometry bit is not provoked: that would take a
-deliberately wrong launch.
+deliberately wrong launch.  The L2 fetch-granularity setting (a
+process-wide CUDA limit) runs in a fresh process of its own.
 """
 import ctypes
 import os
@@ -113,3 +114,33 @@ def test_batch_pool_failure_leaks_nothing(torch_cuda):
     out = subprocess.run([sys.executable, "-c", POOL_SCRIPT % ROOT], capture_output=True, text=True,
                          timeout=300)
     assert out.returncode == 0 and "pool ok" in out.stdout, out.stdout + out.stderr
+
+
+L2_SCRIPT = r"""
+import sys
+sys.path.insert(0, %r)
+import torch
+from paper_2105_10332_b300 import sweep as S, workloads as W
+out = {}
+for setting in (0, 32):
+    dt, dx = W.heat_dt(256, 0.1)
+    h = S.Solver("heat", 256, 256, dt, dx, 64, 30, l2_fetch_bytes=setting)
+    u = torch.from_numpy(W.heat_modes(256, 256, seed=4)).cuda()
+    h.run_swept(u, 23)
+    q0, ex = W.vortex(128)
+    edt, _ = W.vortex_dt(q0, ex, 1.0)
+    e = S.Solver("euler", 128, 128, edt, ex, 32, 6, l2_fetch_bytes=setting)
+    q = torch.from_numpy(q0).cuda()
+    e.run_swept(q, 9)
+    torch.cuda.synchronize()
+    out[setting] = (u.cpu(), q.cpu())
+    assert e.get("l2_fetch_bytes") == setting
+assert torch.equal(out[0][0], out[32][0]) and torch.equal(out[0][1], out[32][1])
+print("l2 ok")
+"""
+
+
+def test_l2_fetch_setting_keeps_the_bits(torch_cuda):
+    out = subprocess.run([sys.executable, "-c", L2_SCRIPT % ROOT], capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0 and "l2 ok" in out.stdout, out.stdout + out.stderr
