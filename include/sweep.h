@@ -35,10 +35,11 @@
  *     Argument and launch errors are returned at once.  What the kernels
  *     find while they run goes to a device error word, the first 4 bytes
  *     of the workspace header, which every run clears on entry: bit
- *     SWEEP_DEV_LAUNCH (a kernel found its grid, block or shared memory
- *     wrong for its geometry; it then does nothing) and bit
- *     SWEEP_DEV_NONFINITE (a state value written to the state array was an
- *     infinity or a NaN, e.g. after a time step beyond the CFL bound).
+ *     SWEEP_DEV_NONFINITE (a value of a run's final state was an infinity
+ *     or a NaN, e.g. after a time step beyond the CFL bound), and, in the
+ *     checked build libsweep_checked.so only, bit SWEEP_DEV_LAUNCH (a kernel
+ *     found its grid, block or shared memory wrong for its geometry; it
+ *     then does nothing).
  *     sweep_check reads it; with the "check" parameter set every run reads
  *     it before returning (and so waits for the GPU).
  *   - Threads: one handle must not be used from two threads at once;

@@ -29,15 +29,27 @@ def deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "sweep.h")]
 
 
+# The checked build: kernels also verify their launch geometry and shared
+# memory at entry and report a mismatch in the device error word.
+LIB_CHECKED = os.path.join(HERE, "libsweep_checked.so")
+
+
 def build(force=False, verbose=False):
-    """Compile libsweep.so if missing or stale; return its path."""
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in deps())):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [NVCC, *FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *sources()]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    """Compile libsweep.so and libsweep_checked.so if missing or stale (both
+    at once); return the path of libsweep.so."""
+    newest = max(os.path.getmtime(f) for f in deps())
+    todo = [(path, extra) for path, extra in ((LIB, []), (LIB_CHECKED, ["-DSWEEP_CHECKED"]))
+            if force or not os.path.exists(path) or os.path.getmtime(path) < newest]
+    procs = []
+    for path, extra in todo:
+        tmp = path + ".tmp%d" % os.getpid()
+        cmd = [NVCC, *FLAGS, *extra, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *sources()]
+        procs.append((subprocess.Popen(cmd), tmp, path))
+    failed = [p.wait() for p, _, _ in procs]
+    if any(failed):
+        raise subprocess.CalledProcessError(max(failed), NVCC)
+    for _, tmp, path in procs:
+        os.replace(tmp, path)
     return LIB
 
 

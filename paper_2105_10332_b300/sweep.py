@@ -11,7 +11,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsweep.so")
+# SWEEP_LIBRARY may name another build of the same library, e.g. the checked
+# build libsweep_checked.so (kernels that also verify their launch geometry)
+LIB_PATH = os.environ.get("SWEEP_LIBRARY") or os.path.join(HERE, "libsweep.so")
 
 SWEEP_HEAT = 0
 SWEEP_EULER = 1

@@ -61,3 +61,21 @@ def test_traffic_needs_a_capture_of_the_current_sources(tmp_path):
 def test_default_workload_is_the_large_heat_grid():
     import bench
     assert bench.DEFAULT_WORKLOAD == "heat16384"
+
+
+def test_roofline_of_the_dominant_kernel(monkeypatch):
+    """achieved = algorithmic flops of one launch of the dominant kernel over its
+    mean live launch time; frac = achieved over the measured FP64 peak."""
+    import bench
+    monkeypatch.setattr(bench, "traffic_per_launch", lambda name, kernel: None)
+    wl = dict(name="heat_x", eqn="heat", nx=256, ny=256, tile=64, depth=30)
+    prof = {"up_pyramid": (0.01, 1), "bridges": (2.0, 4), "octahedron": (3.0, 4),
+            "down_pyramid": (0.2, 1), "standard": (0.0, 0)}
+    fp64 = {"peak_tflops": 1.2}
+    r = bench.roofline(wl, prof, fp64)
+    assert r["kernel"] == "octahedron" and r["bound"] == "alu" and r["traffic"] is None
+    flops = bench.shape_cells("heat", 64, 30, "octahedron", 16) * 7
+    assert r["flops_per_launch"] == flops
+    assert abs(r["achieved"] - flops / 0.75e-3 / 1e12) < 1e-4
+    assert abs(r["frac"] - r["achieved"] / 1.2) < 1e-4
+    assert "hbm" not in r

@@ -144,3 +144,39 @@ def test_l2_fetch_setting_keeps_the_bits(torch_cuda):
     out = subprocess.run([sys.executable, "-c", L2_SCRIPT % ROOT], capture_output=True, text=True,
                          timeout=300)
     assert out.returncode == 0 and "l2 ok" in out.stdout, out.stdout + out.stderr
+
+
+CHECKED_SCRIPT = r"""
+import sys
+sys.path.insert(0, %r)
+import numpy as np, torch
+import oracle
+from paper_2105_10332_b300 import sweep as S, workloads as W
+assert S.LIB_PATH.endswith("libsweep_checked.so")
+dt, dx = W.heat_dt(64, 0.1)
+h = S.Solver("heat", 64, 64, dt, dx, 16, 6, check=1)
+u0 = W.heat_modes(64, 64, seed=9)
+for method in ("run_swept", "run_standard"):
+    u = torch.from_numpy(u0).cuda()
+    getattr(h, method)(u, 13)
+    assert np.array_equal(u.cpu().numpy(), oracle.heat_run(u0, 13, dt, dx)), method
+q0, ex = W.vortex(64)
+edt, _ = W.vortex_dt(q0, ex, 1.0)
+e = S.Solver("euler", 64, 64, edt, ex, 32, 6, check=1)
+for method in ("run_swept", "run_standard"):
+    q = torch.from_numpy(q0).cuda()
+    getattr(e, method)(q, 7)
+    assert np.array_equal(q.cpu().numpy(), oracle.euler_run(q0, edt, ex, 7)), method
+print("checked ok")
+"""
+
+
+def test_checked_build_verifies_its_launches(torch_cuda):
+    """The checked build (every kernel verifies its grid, block and shared
+    memory at entry) runs the same bits as the oracle with "check" set, so
+    every run reads back a clear device error word."""
+    from paper_2105_10332_b300 import build
+    env = dict(os.environ, SWEEP_LIBRARY=build.LIB_CHECKED)
+    out = subprocess.run([sys.executable, "-c", CHECKED_SCRIPT % ROOT], capture_output=True,
+                         text=True, timeout=300, env=env)
+    assert out.returncode == 0 and "checked ok" in out.stdout, out.stdout + out.stderr
