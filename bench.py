@@ -16,6 +16,7 @@ carries the Euler vortex at 256 x 256 advanced to t = 10 (2999 steps, block
   python bench.py --peaks                      # the FP64 probe alone
   python bench.py --workload heat16384|heat64|euler256 --sweep
         # the block-size sweep (tile edge x depth x cluster), one line each
+  python bench.py ... --l2-fetch 0|32|64|128   # the L2 fetch limit (default 32)
   python bench.py --workload W --ncu-run swept|standard
         # W warm-up runs then one run, nothing timed: the command that the
         # ncu captures summarised under profiles/ run
@@ -808,7 +809,11 @@ def main():
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--ncu-run", choices=["swept", "standard"], default=None)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--l2-fetch", type=int, choices=[0, 32, 64, 128], default=32,
+                    help="L2 fetch-granularity limit the solvers set for the process "
+                         "(0: leave the context's default)")
     args = ap.parse_args()
+    BENCH_PARAMS["l2_fetch_bytes"] = args.l2_fetch
     if args.peaks:
         run_peaks(args)
         return
