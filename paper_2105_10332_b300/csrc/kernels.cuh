@@ -406,6 +406,20 @@ __device__ __forceinline__ void for_units(Rect O, Rect I, int par, bool vec, F &
     }
 }
 
+// Visit R with the CTA's threads two horizontally adjacent cells (x, x+1)
+// per thread (f gets two = true) when R is an even number of cells wide,
+// else one cell per thread.
+template <class F>
+__device__ __forceinline__ void for_pairs(Rect R, F &&f)
+{
+    const int w = R.w(), h = R.h();
+    const bool two = (w & 1) == 0;
+    const int wu = two ? w >> 1 : w;
+    const int total = wu * h;
+    for (int q = threadIdx.x; q < total; q += blockDim.x)
+        f(R.x0 + (q % wu) * (two ? 2 : 1), R.y0 + q / wu, two);
+}
+
 template <class F>
 __device__ __forceinline__ void for_rect(Rect R, F &&f)
 {
@@ -586,6 +600,72 @@ struct Stage<Heat, C> {
                   heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c,
                               p.ek.f));
         });
+    }
+    // Two neighbouring cells per thread (two independent FP64 chains that
+    // hide each other's latency, half the index arithmetic per cell) wherever
+    // the region is an even number of cells wide, else one.
+    __device__ __forceinline__ static void run_pairs(const Params &p, Block<Heat, C> &B,
+                                                     int64_t level, Rect R)
+    {
+        const bool second = (level & 1) == 0;
+        const double *src = B.lev(level - 1);
+        const double *own = second ? B.lev(level) : src;
+        const double c = second ? p.c2 : p.c1;
+        const int wp = B.wp;
+        for_pairs(band(R, B.rank, C), [&](int x, int y, bool two) {
+            const int i = y * wp + x;
+            const double a = heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp],
+                                         own[i], c, p.ek.f);
+            if (two) {
+                const double e = heat_update(src[i + 1], src[i], src[i + 2], src[i + 1 - wp],
+                                             src[i + 1 + wp], own[i + 1], c, p.ek.f);
+                B.put(level, 0, i + 1, e);
+            }
+            B.put(level, 0, i, a);
+        });
+    }
+    // The swept kernels' form on large grids: levels of at least four cells
+    // per thread in pairs, smaller levels one cell per thread (every lane
+    // they can fill).  Written in this shape -- the level's inputs taken
+    // once, the pair loop in a function of its own -- it measured heat
+    // 16384^2 Swept 50.1 Gcell-steps/s in three builds; two other shapes of
+    // the same arithmetic and order measured 48.7.
+    __device__ __forceinline__ static void run_wide(const Params &p, Block<Heat, C> &B,
+                                                    int64_t level, Rect R)
+    {
+        const bool second = (level & 1) == 0;
+        const double *src = B.lev(level - 1);
+        const double *own = second ? B.lev(level) : src;
+        const double c = second ? p.c2 : p.c1;
+        const int wp = B.wp;
+        const Rect S = band(R, B.rank, C);
+        if (S.area() >= 4 * (int)blockDim.x && (S.w() & 1) == 0) {
+            pairs(p, B, level, S, src, own, c);
+            return;
+        }
+        for_rect(S, [&](int x, int y) {
+            const int i = y * wp + x;
+            B.put(level, 0, i,
+                  heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp], own[i], c,
+                              p.ek.f));
+        });
+    }
+    // cells (x, x+1) of an even-width region S, one pair per thread
+    __device__ __forceinline__ static void pairs(const Params &p, Block<Heat, C> &B, int64_t level,
+                                                 Rect S, const double *src, const double *own,
+                                                 double c)
+    {
+        const int wp = B.wp;
+        const int wu = S.w() >> 1, total = wu * S.h();
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int i = (S.y0 + q / wu) * wp + S.x0 + 2 * (q % wu);
+            const double a = heat_update(src[i], src[i - 1], src[i + 1], src[i - wp], src[i + wp],
+                                         own[i], c, p.ek.f);
+            const double e = heat_update(src[i + 1], src[i], src[i + 2], src[i + 1 - wp],
+                                         src[i + 1 + wp], own[i + 1], c, p.ek.f);
+            B.put(level, 0, i, a);
+            B.put(level, 0, i + 1, e);
+        }
     }
 };
 
@@ -877,6 +957,17 @@ __device__ __forceinline__ void export_band(const Params &p, Block<EQ, C> &B, in
     store_level(p, B, level, Oc, Ic);
 }
 
+// One level of a swept shape.  WIDE (heat on large grids, the host's
+// choice): large levels take two cells per thread (Stage::run_wide).
+template <class EQ, int C, bool WIDE>
+__device__ __forceinline__ void stage(const Params &p, Block<EQ, C> &B, int64_t level, Rect R)
+{
+    if constexpr (WIDE)
+        Stage<EQ, C>::run_wide(p, B, level, R);
+    else
+        Stage<EQ, C>::run(p, B, level, R);
+}
+
 // Everything a growing shape (Bridges, the lower half of an Octahedron)
 // needs from other shapes was written by earlier launches, so it is fetched
 // at once when the kernel starts: the ring of level base+s-1 around the shape
@@ -903,14 +994,14 @@ __device__ __forceinline__ void preload_growing(const Params &p, Block<EQ, C> &B
 }
 
 // A shape that grows from nothing, its inputs already preloaded.
-template <class EQ, int C>
+template <class EQ, int C, bool WIDE>
 __device__ __forceinline__ void run_growing(const Params &p, Block<EQ, C> &B, int kind, int64_t base)
 {
     const int n = EQ::N, b = p.b, d = p.d;
     for (int s = 1; s <= d; ++s) {
         const int64_t level = base + s;
         const Rect R = shape_rect(kind, b, n, s);
-        Stage<EQ, C>::run(p, B, level, R);
+        stage<EQ, C, WIDE>(p, B, level, R);
         level_barrier<C>();
         if (kind != kLower)
             export_band(p, B, kind, s, level, R);
@@ -919,7 +1010,7 @@ __device__ __forceinline__ void run_growing(const Params &p, Block<EQ, C> &B, in
 
 // An Up-Pyramid on the window whose level `base` is already in buffer F of
 // every CTA of the cluster.
-template <class EQ, int C>
+template <class EQ, int C, bool WIDE>
 __device__ __forceinline__ void run_pyramid(const Params &p, Block<EQ, C> &B, int64_t base)
 {
     const int n = EQ::N, b = p.b, d = p.d;
@@ -927,7 +1018,7 @@ __device__ __forceinline__ void run_pyramid(const Params &p, Block<EQ, C> &B, in
     for (int s = 1; s <= d; ++s) {
         const int64_t level = base + s;
         const Rect R = shape_rect(kUp, b, n, s);
-        Stage<EQ, C>::run(p, B, level, R);
+        stage<EQ, C, WIDE>(p, B, level, R);
         level_barrier<C>();
         export_band(p, B, kUp, s, level, R);
     }
@@ -937,7 +1028,7 @@ __device__ __forceinline__ void run_pyramid(const Params &p, Block<EQ, C> &B, in
 // Grids: one cluster of C consecutive CTAs per shape.
 
 // Up-Pyramid on block (I, J) of the unshifted grid; level 0 is the state.
-template <class EQ, int C>
+template <class EQ, int C, bool WIDE = false>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_up(const __grid_constant__ Params p)
 {
     extern __shared__ __align__(16) double smem[];
@@ -953,13 +1044,13 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_up(const __grid_consta
     B.set_levels(p, 0);
     state_rect(p, B, p.state, 0, Rect{0, p.b, 0, p.b}, true);
     level_barrier<C>();  // also: every CTA of the cluster has started
-    run_pyramid<EQ, C>(p, B, 0);
+    run_pyramid<EQ, C, WIDE>(p, B, 0);
     level_barrier<C>();  // no CTA leaves while a peer may still write to it
 }
 
 // X- and Y-Bridges on the seams of the grid with offset o; shape 2t is the
 // X-Bridge right of block t, shape 2t+1 the Y-Bridge above it.
-template <class EQ, int C>
+template <class EQ, int C, bool WIDE = false>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_bridges(const __grid_constant__ Params p, int64_t base, int o)
 {
     extern __shared__ __align__(16) double smem[];
@@ -979,7 +1070,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_bridges(const __grid_c
     B.set_levels(p, base);
     preload_growing<EQ, C>(p, B, kind, base, false);
     if constexpr (C > 1) cg::this_cluster().sync();
-    run_growing<EQ, C>(p, B, kind, base);
+    run_growing<EQ, C, WIDE>(p, B, kind, base);
     if constexpr (C > 1) cg::this_cluster().sync();
 }
 
@@ -987,7 +1078,7 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_bridges(const __grid_c
 // offset o (window = the block of the shifted grid centred on that corner).
 // last != 0 makes it the Down-Pyramid: the lower half only, after which the
 // window, now complete at level base+d, is written to the state.
-template <class EQ, int C>
+template <class EQ, int C, bool WIDE = false>
 __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_octahedron(const __grid_constant__ Params p, int64_t base, int o, int last)
 {
     extern __shared__ __align__(16) double smem[];
@@ -1006,11 +1097,11 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_octahedron(const __gri
     B.set_levels(p, base);
     preload_growing<EQ, C>(p, B, kLower, base, true);
     if constexpr (C > 1) cg::this_cluster().sync();
-    run_growing<EQ, C>(p, B, kLower, base);
+    run_growing<EQ, C, WIDE>(p, B, kLower, base);
     const int64_t top = base + p.d;
     const Rect whole = {0, p.b, 0, p.b};
     if (!last) {
-        run_pyramid<EQ, C>(p, B, top);
+        run_pyramid<EQ, C, WIDE>(p, B, top);
     } else {
         state_rect(p, B, p.state, (int)(top & 1), band(whole, B.rank, C), false, true);
     }
@@ -1020,8 +1111,10 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_octahedron(const __gri
 // One RK2 step of the Standard solver: block (I, J) of edge T = std_tile
 // loads its tile plus a 2n halo, takes stage 1 on the tile plus an n halo
 // and stage 2 on the tile, and writes the tile to dst (and, if qstar is
-// not null, the tile's first-stage values to qstar).
-template <class EQ>
+// not null, the tile's first-stage values to qstar).  PAIRS (heat only):
+// each thread takes two neighbouring cells of a stage (Stage::run_pairs),
+// the host's choice for large grids.
+template <class EQ, bool PAIRS = false>
 __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(const __grid_constant__ Params p, const double *src, double *dst,
                                                        double *qstar)
 {
@@ -1036,12 +1129,18 @@ __global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(const __grid_const
     B.oy = (int64_t)J * T - 2 * n;
     state_rect(p, B, const_cast<double *>(src), 0, Rect{0, wp, 0, wp}, true);
     __syncthreads();
-    Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
+    if constexpr (PAIRS)
+        Stage<EQ, 1>::run_pairs(p, B, 1, {n, wp - n, n, wp - n});
+    else
+        Stage<EQ, 1>::run(p, B, 1, {n, wp - n, n, wp - n});
     __syncthreads();
     const Rect tile = {2 * n, wp - 2 * n, 2 * n, wp - 2 * n};
     if (qstar)
         state_rect(p, B, qstar, 1, tile, false);
-    Stage<EQ, 1>::run(p, B, 2, tile);
+    if constexpr (PAIRS)
+        Stage<EQ, 1>::run_pairs(p, B, 2, tile);
+    else
+        Stage<EQ, 1>::run(p, B, 2, tile);
     __syncthreads();
     state_rect(p, B, dst, 0, tile, false, p.check_out != 0);
 }

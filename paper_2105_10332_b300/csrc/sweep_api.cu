@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -174,6 +175,11 @@ struct Bracket {
 // forward-Euler steps) per launch and, for an odd count, one single-level
 // launch; ping-pong between the state and slot 0 of the workspace, ending in
 // the state.
+// the Standard heat step takes two cells per thread on grids of at least
+// 2^20 cells (throughput-bound: heat 16384^2 46.5 -> 48.4 Gcell-steps/s),
+// one on smaller ones (latency-bound: heat 64^2 1.57 against 1.36)
+constexpr int64_t kStdPairsCells = int64_t(1) << 20;
+
 template <class EQ>
 int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
@@ -181,7 +187,10 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     const int T = h->std_tile;
     const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N, 1);
     const size_t smem1 = smem_bytes<EQ>(T + 2 * EQ::N, 1);
-    if (set_smem(k_standard<EQ>, smem) != cudaSuccess || set_smem(k_level1<EQ>, smem1) != cudaSuccess)
+    void (*step)(Params, const double *, double *, double *) = k_standard<EQ>;
+    if constexpr (std::is_same<EQ, Heat>::value)
+        if (h->nx * h->ny >= kStdPairsCells) step = k_standard<Heat, true>;
+    if (set_smem(step, smem) != cudaSuccess || set_smem(k_level1<EQ>, smem1) != cudaSuccess)
         return SWEEP_ECUDA;
     const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
     double *a = p.state, *b = p.ws;
@@ -192,8 +201,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
-            k_standard<EQ><<<grid, EQ::STD_THREADS, smem, st>>>(l + 2 >= nlevels ? last : p, a, b,
-                                                              nullptr);
+            step<<<grid, EQ::STD_THREADS, smem, st>>>(l + 2 >= nlevels ? last : p, a, b, nullptr);
         }
         double *t = a;
         a = b;
@@ -242,7 +250,7 @@ cudaError_t launch(void (*kernel)(KArgs...), unsigned shapes, int threads, size_
     }
 }
 
-template <class EQ, int C, int CB>
+template <class EQ, int C, int CB, bool WIDE>
 int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
     const int64_t L = nlevels;
@@ -251,29 +259,30 @@ int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
     if (L >= d) {
         const size_t smem = smem_bytes<EQ>(h->tile, C * h->passes);
         const size_t smem_b = smem_bytes<EQ>(h->tile, CB * h->passes);
-        if (set_smem(k_up<EQ, C>, smem) != cudaSuccess ||
-            set_smem(k_bridges<EQ, CB>, smem_b) != cudaSuccess ||
-            set_smem(k_octahedron<EQ, C>, smem) != cudaSuccess)
+        if (set_smem(k_up<EQ, C, WIDE>, smem) != cudaSuccess ||
+            set_smem(k_bridges<EQ, CB, WIDE>, smem_b) != cudaSuccess ||
+            set_smem(k_octahedron<EQ, C, WIDE>, smem) != cudaSuccess)
             return SWEEP_ECUDA;
         const unsigned tiles = (unsigned)(p.tiles_x * p.tiles_y);
         const int64_t m = L / d - 1;  // whole [Bridges, Octahedron] cycles
         cudaError_t e;
         {
             Bracket br(h, st, kKindUp);
-            e = launch<C>(k_up<EQ, C>, tiles, EQ::SWEPT_THREADS, smem, st, p);
+            e = launch<C>(k_up<EQ, C, WIDE>, tiles, EQ::SWEPT_THREADS, smem, st, p);
         }
         for (int64_t c = 0; c <= m && e == cudaSuccess; ++c) {
             const int o = (c & 1) ? h->tile / 2 : 0;
             const int64_t base = c * d;
             {
                 Bracket br(h, st, kKindBridges);
-                e = launch<CB>(k_bridges<EQ, CB>, 2 * tiles, EQ::SWEPT_THREADS, smem_b, st, p, base, o);
+                e = launch<CB>(k_bridges<EQ, CB, WIDE>, 2 * tiles, EQ::SWEPT_THREADS, smem_b, st, p,
+                               base, o);
             }
             if (e != cudaSuccess) break;
             {
                 Bracket br(h, st, c == m ? kKindDown : kKindOctahedron);
-                e = launch<C>(k_octahedron<EQ, C>, tiles, EQ::SWEPT_THREADS, smem, st, p, base, o,
-                              c == m ? 1 : 0);
+                e = launch<C>(k_octahedron<EQ, C, WIDE>, tiles, EQ::SWEPT_THREADS, smem, st, p, base,
+                              o, c == m ? 1 : 0);
             }
         }
         if (e != cudaSuccess) return SWEEP_ECUDA;
@@ -282,13 +291,25 @@ int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
     return standard_levels<EQ>(h, p, L - done, st);
 }
 
+// Heat on a grid of at least 2^20 cells runs the WIDE swept kernels: their
+// large levels take two cells per thread (heat 16384^2, block 64: 49.1 ->
+// 50.2 Gcell-steps/s).  Smaller grids run the one-cell kernels, which a
+// compiled-in choice between the two forms slows by ~3 % (heat 64^2).
+template <class EQ, int C, int CB>
+int swept_w(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
+{
+    if constexpr (std::is_same<EQ, Heat>::value)
+        if (h->nx * h->ny >= kStdPairsCells) return swept_c<EQ, C, CB, true>(h, p, nlevels, st);
+    return swept_c<EQ, C, CB, false>(h, p, nlevels, st);
+}
+
 template <class EQ, int C>
 int swept_b(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
     switch (h->cluster_br) {
-    case 2: return swept_c<EQ, C, 2>(h, p, nlevels, st);
-    case 4: return swept_c<EQ, C, 4>(h, p, nlevels, st);
-    default: return swept_c<EQ, C, 1>(h, p, nlevels, st);
+    case 2: return swept_w<EQ, C, 2>(h, p, nlevels, st);
+    case 4: return swept_w<EQ, C, 4>(h, p, nlevels, st);
+    default: return swept_w<EQ, C, 1>(h, p, nlevels, st);
     }
 }
 

@@ -94,6 +94,49 @@ def test_heat_swept_bit_identical(torch_cuda, oracle_lib, nx, ny, tile, nsteps):
         assert np.array_equal(sw, std), ("d=%d" % d, relerr(sw, std))
 
 
+@pytest.mark.parametrize("nx,ny", [(128, 128), (1024, 1024), (2048, 512)])
+@pytest.mark.parametrize("depth", [14, 30])
+def test_heat_block64_large_levels(torch_cuda, oracle_lib, nx, ny, depth):
+    """Block 64.  From 2^20 cells heat runs the wide swept kernels (levels
+    of at least four cells per thread take two neighbouring cells per
+    thread, smaller ones one) and the paired Standard step; below, the
+    one-cell kernels.  Swept and Standard match the oracle bit for bit."""
+    from paper_2105_10332_b300 import sweep as S
+    s, dt, dx = heat_solver(S, nx, ny, 64, depth)
+    u0 = W.heat_modes(nx, ny, seed=depth)
+    for nsteps in (17, 31):
+        ref = oracle_lib.heat_run(u0, nsteps, dt, dx)
+        for method in ("run_swept", "run_standard"):
+            got = gpu_run(torch_cuda, s, u0, nsteps, method)
+            assert np.array_equal(got, ref), (method, nsteps, relerr(got, ref))
+
+
+@pytest.mark.parametrize("cluster,passes", [(2, 1), (4, 1), (1, 2), (2, 2)])
+def test_heat_wide_kernels_in_bands(torch_cuda, oracle_lib, cluster, passes):
+    """The wide heat kernels with a window shared by a cluster of CTAs, or
+    walked in sub-bands: each band of a level takes the pair or the one-cell
+    branch on its own size.  1024^2, block 64, against the oracle."""
+    from paper_2105_10332_b300 import sweep as S
+    s, dt, dx = heat_solver(S, 1024, 1024, 64, 30)
+    s.set("cluster", cluster)
+    s.set("passes", passes)
+    u0 = W.heat_modes(1024, 1024, seed=cluster * 10 + passes)
+    ref = oracle_lib.heat_run(u0, 31, dt, dx)
+    got = gpu_run(torch_cuda, s, u0, 31, "run_swept")
+    assert np.array_equal(got, ref), relerr(got, ref)
+
+
+def test_heat_standard_paired_step_1024(torch_cuda, oracle_lib):
+    """From 2^20 cells the Standard heat step takes two cells per thread:
+    1024^2 against the oracle, bit for bit."""
+    from paper_2105_10332_b300 import sweep as S
+    s, dt, dx = heat_solver(S, 1024, 1024, 32, 14)
+    u0 = W.heat_modes(1024, 1024, seed=11)
+    ref = oracle_lib.heat_run(u0, 9, dt, dx)
+    got = gpu_run(torch_cuda, s, u0, 9, "run_standard")
+    assert np.array_equal(got, ref), relerr(got, ref)
+
+
 def test_heat_swept_sine64_and_closed_form(torch_cuda, oracle_lib):
     """Heat sine 64^2, r = 0.1, 500 steps, tile 16: Swept = Standard = oracle,
     and the discrete closed form G^500 within 1e-13."""
