@@ -394,35 +394,9 @@ def run_adjoint(args, wl):
     if dist_setup()[1] != 0:
         return  # a single-GPU measurement: under torchrun rank 0 alone runs it
     import torch
-    from paper_2105_10332_b300 import sweep as S
     dev = torch.device("cuda", torch.cuda.current_device())
-    solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"],
-                      limiter=wl.get("limiter", 0))
     N, cells = wl["nsteps"], wl["nx"] * wl["ny"]
-    q0 = torch.from_numpy(wl["state"]).to(dev)
-    target = torch.from_numpy(wl["target"]).to(dev)
-    qN = q0.clone()
-    solver.run_swept(qN, N)
-    lamT = torch.zeros_like(q0)
-    lamT[0] = 2.0 * (qN[0] - target)
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        solver.adjoint(q0, lamT, N, wl["ckpt"])
-    torch.cuda.synchronize(dev)
-    a0, a1 = ev(), ev()
-    a0.record()
-    for _ in range(args.steps):
-        g = solver.adjoint(q0, lamT, N, wl["ckpt"])
-    a1.record()
-    torch.cuda.synchronize(dev)
-    ms_adj = a0.elapsed_time(a1) / args.steps
-    f0, f1 = ev(), ev()
-    q = q0.clone()
-    f0.record()
-    solver.run_swept(q, N)
-    f1.record()
-    torch.cuda.synchronize(dev)
-    ms_fwd = f0.elapsed_time(f1)
+    ms_adj, ms_fwd, gnorm = measure_adjoint(wl, dev, args.warmup, args.steps)
     line = {"metric": "Gcell-steps/s of the discrete adjoint (FP64, 1 B300)",
             "value": round(cells * N / (ms_adj / 1e3) / 1e9, 6), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_adj, 3),
@@ -431,8 +405,42 @@ def run_adjoint(args, wl):
             "config": {"workload": wl["name"], "nx": wl["nx"], "ny": wl["ny"], "steps_per_run": N,
                        "ckpt_every": wl["ckpt"], "tile": wl["tile"], "depth": wl["depth"]},
             "forward_ms": round(ms_fwd, 3), "adjoint_over_forward": round(ms_adj / ms_fwd, 3),
-            "grad_norm": float(torch.linalg.vector_norm(g))}
+            "grad_norm": gnorm}
     print(json.dumps(line), flush=True)
+
+
+def measure_adjoint(wl, dev, warmup, steps):
+    """Milliseconds of one gradient (mean of `steps` sweep_adjoint calls after
+    `warmup`), of one plain swept forward run, and the gradient's norm."""
+    import torch
+    from paper_2105_10332_b300 import sweep as S
+    solver = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"],
+                      limiter=wl.get("limiter", 0))
+    N = wl["nsteps"]
+    q0 = torch.from_numpy(wl["state"]).to(dev)
+    target = torch.from_numpy(wl["target"]).to(dev)
+    qN = q0.clone()
+    solver.run_swept(qN, N)
+    lamT = torch.zeros_like(q0)
+    lamT[0] = 2.0 * (qN[0] - target)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        solver.adjoint(q0, lamT, N, wl["ckpt"])
+    torch.cuda.synchronize(dev)
+    a0, a1 = ev(), ev()
+    a0.record()
+    for _ in range(steps):
+        g = solver.adjoint(q0, lamT, N, wl["ckpt"])
+    a1.record()
+    torch.cuda.synchronize(dev)
+    ms_adj = a0.elapsed_time(a1) / steps
+    f0, f1 = ev(), ev()
+    q = q0.clone()
+    f0.record()
+    solver.run_swept(q, N)
+    f1.record()
+    torch.cuda.synchronize(dev)
+    return ms_adj, f0.elapsed_time(f1), float(torch.linalg.vector_norm(g))
 
 
 def measure_fp64(dev, target_s=0.25, launches=5):
@@ -684,6 +692,20 @@ def run_sweep(args, wl):
         torch.cuda.empty_cache()
 
 
+def paired_extra(name, dev, fp64, K):
+    """Swept against Standard on another workload: K whole runs of each."""
+    w = workload(name)
+    r = Runner(w, dev)
+    r.warm("run_swept", 3)
+    r.warm("run_standard", 3)
+    vs = job_rate(1, r.cells, r.N, K, r.timed("run_swept", K) / 1e3)
+    vt = job_rate(1, r.cells, r.N, K, r.timed("run_standard", K) / 1e3)
+    roof = roofline(w, r.profile(), fp64)
+    roof.pop("fp64_probe")
+    return {"workload": w["name"], "runs": K, "swept": round(vs, 6), "standard": round(vt, 6),
+            "swept_over_standard": round(vs / vt, 4), "roofline": roof}
+
+
 def run_ours(args, wl):
     import torch
     world, rank, local = dist_setup()
@@ -749,25 +771,20 @@ def run_ours(args, wl):
     line = None
     if rank == 0:
         extras = {}
-        if wl["name"] != workload("euler256")["name"]:
-            # the Euler vortex at 256^2, t = 10: Swept against Standard on the
-            # same protocol (graph replay, L2 flushed), as extra keys
-            ew = workload("euler256")
-            er = Runner(ew, dev)
-            er.warm("run_swept", 3)
-            er.warm("run_standard", 3)
-            Ke = max(1, min(K, 5))
-            es = er.timed("run_swept", Ke)
-            et = er.timed("run_standard", Ke)
-            eprof = er.profile()
-            vs = job_rate(1, er.cells, er.N, Ke, es / 1e3)
-            vt = job_rate(1, er.cells, er.N, Ke, et / 1e3)
-            eroof = roofline(ew, eprof, fp64)
-            eroof.pop("fp64_probe")
-            extras["euler256"] = {"workload": ew["name"], "runs": Ke, "swept": round(vs, 6),
-                                  "standard": round(vt, 6), "swept_over_standard": round(vs / vt, 4),
-                                  "roofline": eroof}
-            del er
+        if wl["name"] == workload(DEFAULT_WORKLOAD)["name"] and not args.no_extras:
+            # the other single-instance workloads under the same clock: the
+            # Euler vortex at 256^2 and heat at 64^2, Swept against Standard
+            # on the same protocol (graph replay, L2 flushed), and one
+            # gradient of the Euler adjoint at 1024^2
+            for key in ("euler256", "heat64"):
+                extras[key] = paired_extra(key, dev, fp64, max(1, min(K, 5)))
+            aw = workload("adjoint1024")
+            ms_adj, ms_fwd, _ = measure_adjoint(aw, dev, 1, 1)
+            extras["adjoint1024"] = {
+                "workload": aw["name"], "gradients": 1,
+                "value": round(aw["nx"] * aw["ny"] * aw["nsteps"] / (ms_adj / 1e3) / 1e9, 6),
+                "gradient_ms": round(ms_adj, 3), "forward_ms": round(ms_fwd, 3),
+                "adjoint_over_forward": round(ms_adj / ms_fwd, 3)}
         os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
         cb_value, cb_steps, cb_secs = oracle_sample(wl, 12.0)
         cpu_baseline = {"value": round(cb_value, 6), "unit": UNIT,
@@ -809,6 +826,8 @@ def main():
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--ncu-run", choices=["swept", "standard"], default=None)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the default workload's line without its extra workloads")
     ap.add_argument("--l2-fetch", type=int, choices=[0, 32, 64, 128], default=32,
                     help="L2 fetch-granularity limit the solvers set for the process "
                          "(0: leave the context's default)")
