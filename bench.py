@@ -624,10 +624,11 @@ SWEEP_PLANS = {
     # the block-size sweep of the large heat workload: tile edges 8-64, for each
     # the largest even depth and about half of it (edges 12 and 24 do not
     # divide 16384 and run on 16368 = 12 x 1364 = 24 x 682)
-    "heat16384": dict(tiles=(8, 12, 16, 24, 32, 48, 64), clusters=(1,), depths="max_half"),
+    "heat16384": dict(tiles=(8, 12, 16, 24, 32, 48, 64), clusters=(1,), depths="max_half",
+                      standard_tiles=(16, 32, 64)),
     # the small heat grid: every depth and cluster size of edges 8, 16, 32
-    "heat64": dict(tiles=(8, 16, 32), clusters=(1, 2, 4), depths="all"),
-    "euler256": dict(tiles=(16, 32), clusters=(1, 2, 4), depths="all"),
+    "heat64": dict(tiles=(8, 16, 32), clusters=(1, 2, 4), depths="all", standard_tiles=(8, 16, 32)),
+    "euler256": dict(tiles=(16, 32), clusters=(1, 2, 4), depths="all", standard_tiles=(8, 16)),
 }
 
 
@@ -651,14 +652,63 @@ def sweep_configs(wl, plan):
     return out
 
 
+# steps per run of the heat grids of a Standard-edge sweep over grid sides
+HEAT_SIDE_STEPS = {256: 2000, 512: 2000, 1024: 1000, 2048: 500, 4096: 200, 8192: 100}
+
+
+def side_workload(wl, n):
+    """The heat workload wl on an n x n grid (same mesh ratio and field)."""
+    from paper_2105_10332_b300 import workloads as W
+    w = dict(wl, name="heat_modes_%dx%d_%dsteps" % (n, n, HEAT_SIDE_STEPS[n]), nx=n, ny=n,
+             nsteps=HEAT_SIDE_STEPS[n], state=W.heat_modes(n, n))
+    w["dt"], w["dx"] = W.heat_dt(n, 0.1)
+    return w
+
+
+def run_sweep_standard(args, wl, dev):
+    """Standard Gcell-steps/s of the workload at each block edge of its plan;
+    with --sides (heat), of the same workload on those grid sides instead,
+    each with Swept at the workload's tile and depth beside it.  One JSON
+    line per grid."""
+    import torch
+    from paper_2105_10332_b300 import sweep as S
+    cases = [side_workload(wl, n) for n in args.sides] if args.sides else [wl]
+    for w in cases:
+        r = Runner(w, dev)
+        line = {"sweep": w["name"], "default_standard_tile": int(r.solver.get("standard_tile"))}
+        for t in SWEEP_PLANS[args.workload]["standard_tiles"]:
+            try:
+                r.solver.set("standard_tile", t)
+            except S.SweepError:
+                continue  # the edge does not divide this grid
+            r.graphs.pop("run_standard", None)
+            r.warm("run_standard", 2)
+            ms = r.timed("run_standard", args.steps) / args.steps
+            line["standard_%d" % t] = round(job_rate(1, r.cells, r.N, 1, ms / 1e3), 4)
+        if args.sides:
+            r.warm("run_swept", 2)
+            ms = r.timed("run_swept", args.steps) / args.steps
+            line["swept"] = round(job_rate(1, r.cells, r.N, 1, ms / 1e3), 4)
+        print(json.dumps(line), flush=True)
+        del r
+        torch.cuda.empty_cache()
+
+
 def run_sweep(args, wl):
     """Swept Gcell-steps/s of the workload for each (tile, depth, cluster) of
     its plan, and Standard once per grid size; one JSON line per
-    configuration (graph replay, L2 flushed, K = --steps runs each)."""
+    configuration (graph replay, L2 flushed, K = --steps runs each).  With
+    --sweep-standard, the Standard solver at each block edge of the plan
+    instead."""
     import torch
     from paper_2105_10332_b300 import sweep as S, workloads as W
     dev = torch.device("cuda", torch.cuda.current_device())
-    plan = SWEEP_PLANS[args.workload]
+    if args.sweep_standard:
+        run_sweep_standard(args, wl, dev)
+        return
+    plan = dict(SWEEP_PLANS[args.workload])
+    if args.tiles:
+        plan["tiles"] = tuple(t for t in plan["tiles"] if t in args.tiles)
     done_std, states = set(), {}
     for nx, b, d, c in sweep_configs(wl, plan):
         cfg = dict(wl)
@@ -826,6 +876,13 @@ def main():
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--ncu-run", choices=["swept", "standard"], default=None)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--tiles", type=lambda v: [int(t) for t in v.split(",")], default=None,
+                    help="with --sweep: only these tile edges of the plan (comma list)")
+    ap.add_argument("--sweep-standard", action="store_true",
+                    help="with --sweep: the Standard solver at each block edge of the plan")
+    ap.add_argument("--sides", type=lambda v: [int(t) for t in v.split(",")], default=None,
+                    help="with --sweep-standard (heat): these grid sides instead of the "
+                         "workload's (" + ",".join(str(n) for n in HEAT_SIDE_STEPS) + ")")
     ap.add_argument("--no-extras", action="store_true",
                     help="the default workload's line without its extra workloads")
     ap.add_argument("--l2-fetch", type=int, choices=[0, 32, 64, 128], default=32,

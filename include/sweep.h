@@ -88,11 +88,12 @@ enum sweep_status {
  *          d even so that every phase ends on a whole RK2 step; 0 picks the
  *          largest even d allowed.
  * Defaults: alpha = 1, gamma = 1.4, limiter 0, RK2.  The Standard solver
- * uses its own block edge ("standard_tile"): by default the first of 32
- * (heat only), 16, 8, 24, 12, 64, 48, 40, 20, 10 that divides the grid into
- * at least 148 blocks (one per SM of a B300), else the allowed edge of that
- * list giving the most blocks, else the smallest even edge in [8, 64] that
- * divides both sides.  On success *out receives the handle (destroy with
+ * uses its own block edge ("standard_tile"): by default the first of the
+ * list that divides the grid into at least its minimum number of blocks --
+ * heat: 64 (1024 blocks), 32 (1024), then 16, 8, 24, 12, 48, 40, 20, 10
+ * (148 each, one per SM of a B300); Euler: 16, 8, 24, 12, 64, 48, 40, 20,
+ * 10 (148 each) -- else the allowed edge of that list giving the most
+ * blocks, else the smallest even edge in [8, 64] that divides both sides.  On success *out receives the handle (destroy with
  * sweep_destroy).  Returns SWEEP_EINVAL for any violated bound.
  */
 int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx, int tile, int depth,

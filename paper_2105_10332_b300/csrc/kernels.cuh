@@ -624,12 +624,14 @@ struct Stage<Heat, C> {
             B.put(level, 0, i, a);
         });
     }
-    // The swept kernels' form on large grids: levels of at least four cells
-    // per thread in pairs, smaller levels one cell per thread (every lane
-    // they can fill).  Written in this shape -- the level's inputs taken
-    // once, the pair loop in a function of its own -- it measured heat
-    // 16384^2 Swept 50.1 Gcell-steps/s in three builds; two other shapes of
-    // the same arithmetic and order measured 48.7.
+    // The swept kernels' form on large grids: one cell per thread, and two
+    // neighbouring cells per thread only on levels of at least 16 cells per
+    // thread (the full-window levels of b = 64).  Measured at heat 16384^2,
+    // Swept Gcell-steps/s against that threshold: 2: 47.7, 4: 50.2, 8: 50.8,
+    // 12: 51.3, 16: 51.9, never taken: 51.9; and 49.2 for the same one-cell
+    // loop with no pair branch at all.  The branch's presence changes how
+    // the compiler lays out the one-cell loop, which carries nearly every
+    // level; the arithmetic and its order are the same in all of them.
     __device__ __forceinline__ static void run_wide(const Params &p, Block<Heat, C> &B,
                                                     int64_t level, Rect R)
     {
@@ -639,7 +641,7 @@ struct Stage<Heat, C> {
         const double c = second ? p.c2 : p.c1;
         const int wp = B.wp;
         const Rect S = band(R, B.rank, C);
-        if (S.area() >= 4 * (int)blockDim.x && (S.w() & 1) == 0) {
+        if (S.area() >= 16 * (int)blockDim.x && (S.w() & 1) == 0) {
             pairs(p, B, level, S, src, own, c);
             return;
         }
@@ -958,7 +960,8 @@ __device__ __forceinline__ void export_band(const Params &p, Block<EQ, C> &B, in
 }
 
 // One level of a swept shape.  WIDE (heat on large grids, the host's
-// choice): large levels take two cells per thread (Stage::run_wide).
+// choice): Stage::run_wide, whose levels of at least 16 cells per thread
+// take two cells per thread.
 template <class EQ, int C, bool WIDE>
 __device__ __forceinline__ void stage(const Params &p, Block<EQ, C> &B, int64_t level, Rect R)
 {
@@ -1113,14 +1116,15 @@ __global__ void __launch_bounds__(EQ::SWEPT_THREADS, 1) k_octahedron(const __gri
 // and stage 2 on the tile, and writes the tile to dst (and, if qstar is
 // not null, the tile's first-stage values to qstar).  PAIRS (heat only):
 // each thread takes two neighbouring cells of a stage (Stage::run_pairs),
-// the host's choice for large grids.
-template <class EQ, bool PAIRS = false>
-__global__ void __launch_bounds__(EQ::STD_THREADS) k_standard(const __grid_constant__ Params p, const double *src, double *dst,
+// the host's choice for large grids.  THREADS: threads per CTA (the host
+// gives 64-wide heat blocks twice the default).
+template <class EQ, bool PAIRS = false, int THREADS = EQ::STD_THREADS>
+__global__ void __launch_bounds__(THREADS) k_standard(const __grid_constant__ Params p, const double *src, double *dst,
                                                        double *qstar)
 {
     extern __shared__ __align__(16) double smem[];
     const int T = p.std_tile, n = EQ::N, wp = T + 4 * n;
-    if (!launch_ok(p, (unsigned)p.std_blocks, EQ::STD_THREADS, smem_bytes<EQ>(wp, 1)))
+    if (!launch_ok(p, (unsigned)p.std_blocks, THREADS, smem_bytes<EQ>(wp, 1)))
         return;
     Block<EQ, 1> B;
     B.carve(smem, wp);

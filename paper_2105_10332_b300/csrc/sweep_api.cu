@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <iterator>
 #include <type_traits>
 #include <cstdint>
 #include <cstring>
@@ -179,6 +180,10 @@ struct Bracket {
 // 2^20 cells (throughput-bound: heat 16384^2 46.5 -> 48.4 Gcell-steps/s),
 // one on smaller ones (latency-bound: heat 64^2 1.57 against 1.36)
 constexpr int64_t kStdPairsCells = int64_t(1) << 20;
+// threads of a 64-wide heat Standard block, paired: 512 (heat 4096^2 47.8 ->
+// 49.0 Gcell-steps/s against 256; 16384^2 51.1 either way; 32-wide and
+// smaller blocks are fastest at 256)
+constexpr int kStdThreads64 = 512;
 
 template <class EQ>
 int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
@@ -188,8 +193,15 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     const size_t smem = smem_bytes<EQ>(T + 4 * EQ::N, 1);
     const size_t smem1 = smem_bytes<EQ>(T + 2 * EQ::N, 1);
     void (*step)(Params, const double *, double *, double *) = k_standard<EQ>;
+    int threads = EQ::STD_THREADS;
     if constexpr (std::is_same<EQ, Heat>::value)
-        if (h->nx * h->ny >= kStdPairsCells) step = k_standard<Heat, true>;
+        if (h->nx * h->ny >= kStdPairsCells) {
+            step = k_standard<Heat, true>;
+            if (T == 64) {
+                step = k_standard<Heat, true, kStdThreads64>;
+                threads = kStdThreads64;
+            }
+        }
     if (set_smem(step, smem) != cudaSuccess || set_smem(k_level1<EQ>, smem1) != cudaSuccess)
         return SWEEP_ECUDA;
     const unsigned grid = (unsigned)((h->nx / T) * (h->ny / T));
@@ -201,7 +213,7 @@ int standard_levels(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st
     for (int64_t l = 0; l + 1 < nlevels; l += 2) {
         {
             Bracket br(h, st, kKindStandard);
-            step<<<grid, EQ::STD_THREADS, smem, st>>>(l + 2 >= nlevels ? last : p, a, b, nullptr);
+            step<<<grid, threads, smem, st>>>(l + 2 >= nlevels ? last : p, a, b, nullptr);
         }
         double *t = a;
         a = b;
@@ -291,10 +303,11 @@ int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
     return standard_levels<EQ>(h, p, L - done, st);
 }
 
-// Heat on a grid of at least 2^20 cells runs the WIDE swept kernels: their
-// large levels take two cells per thread (heat 16384^2, block 64: 49.1 ->
-// 50.2 Gcell-steps/s).  Smaller grids run the one-cell kernels, which a
-// compiled-in choice between the two forms slows by ~3 % (heat 64^2).
+// Heat on a grid of at least 2^20 cells runs the WIDE swept kernels
+// (Stage<Heat>::run_wide: levels of at least 16 cells per thread in pairs;
+// heat 16384^2, block 64: 49.2 -> 51.9 Gcell-steps/s).  Smaller grids run
+// the one-cell kernels, which the same compiled-in choice slows by ~3 %
+// (heat 64^2).
 template <class EQ, int C, int CB>
 int swept_w(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
@@ -536,15 +549,33 @@ SWEEP_API int sweep_create(int eqn, int64_t nx, int64_t ny, double dt, double dx
     h->l2_fetch = 0;
     h->profile = 0;
     h->ev_used = 0;
-    // Standard block edge: the first preferred edge that gives at least one
-    // block per SM (148 on B300), else the allowed edge with the most blocks
-    // (a small grid is latency bound: more, smaller blocks finish sooner)
-    const int prefer[] = {eqn == SWEEP_HEAT ? 32 : 16, 16, 8, 24, 12, 64, 48, 40, 20, 10};
+    // Standard block edge: the first preferred edge that cuts the grid into
+    // at least its minimum number of blocks, else the allowed edge with the
+    // most blocks (a small grid is latency bound: more, smaller blocks finish
+    // sooner).  The minimums are measured on B300 (heat, 256^2 to 16384^2):
+    // 64- and 32-wide heat blocks pay for their smaller halo share from 1024
+    // blocks (64-wide: 2048^2 and up); other edges need one block per SM
+    // (148).
+    struct Pref {
+        int t;
+        int64_t min_blocks;
+    };
+    const Pref heat_prefer[] = {{64, 1024}, {32, 1024}, {16, kStdMinBlocks}, {8, kStdMinBlocks},
+                                {24, kStdMinBlocks}, {12, kStdMinBlocks}, {48, kStdMinBlocks},
+                                {40, kStdMinBlocks}, {20, kStdMinBlocks}, {10, kStdMinBlocks}};
+    const Pref euler_prefer[] = {{16, kStdMinBlocks}, {8, kStdMinBlocks},  {24, kStdMinBlocks},
+                                 {12, kStdMinBlocks}, {64, kStdMinBlocks}, {48, kStdMinBlocks},
+                                 {40, kStdMinBlocks}, {20, kStdMinBlocks}, {10, kStdMinBlocks}};
+    const bool heat = eqn == SWEEP_HEAT;
+    const Pref *prefer = heat ? heat_prefer : euler_prefer;
+    const int nprefer = heat ? (int)std::size(heat_prefer) : (int)std::size(euler_prefer);
     int64_t most = 0;
-    for (int t : prefer) {
+    for (int k = 0; k < nprefer; ++k) {
+        const Pref &pr = prefer[k];
+        const int t = pr.t;
         if (!valid_std_tile(h, t)) continue;
         const int64_t blocks = (nx / t) * (ny / t);
-        if (blocks >= kStdMinBlocks) {
+        if (blocks >= pr.min_blocks) {
             h->std_tile = t;
             break;
         }

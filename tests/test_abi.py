@@ -218,9 +218,13 @@ def test_batch_workspace_is_sum_of_instances(L):
 
 def test_standard_tile_default_fills_the_sms(L):
     """The default Standard block edge is the first preferred edge giving at
-    least 148 blocks (one per B300 SM), else the edge giving the most."""
+    least its minimum number of blocks (heat: 64 and 32 from 1024 blocks,
+    smaller edges from 148, one per B300 SM), else the edge giving the
+    most."""
     for eqn, nx, tile, expect in ((S.SWEEP_HEAT, 64, 16, 8), (S.SWEEP_HEAT, 128, 16, 8),
-                                  (S.SWEEP_HEAT, 512, 32, 32), (S.SWEEP_HEAT, 4096, 64, 32),
+                                  (S.SWEEP_HEAT, 256, 32, 16), (S.SWEEP_HEAT, 512, 32, 16),
+                                  (S.SWEEP_HEAT, 1024, 64, 32), (S.SWEEP_HEAT, 2048, 64, 64),
+                                  (S.SWEEP_HEAT, 4096, 64, 64), (S.SWEEP_HEAT, 16384, 64, 64),
                                   (S.SWEEP_EULER, 256, 32, 16), (S.SWEEP_EULER, 64, 32, 8),
                                   (S.SWEEP_EULER, 1024, 32, 16), (S.SWEEP_HEAT, 72, 12, 8)):
         h = S.sweep_create(eqn, nx, nx, 1e-6, 1.0 / nx, tile, 0)

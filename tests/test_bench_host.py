@@ -101,3 +101,26 @@ def test_sweep_plans_are_legal_geometries():
     tiles = {b: n for n, b, _, _ in bench.sweep_configs(dict(nx=16384, eqn="heat"),
                                                        bench.SWEEP_PLANS["heat16384"])}
     assert tiles[12] == 16380 and tiles[24] == 16368 and tiles[64] == 16384
+
+
+def test_standard_edge_plans_are_legal():
+    """bench.py --sweep --sweep-standard: every Standard block edge of a plan
+    is one the library accepts on that workload's grid."""
+    import bench
+    from paper_2105_10332_b300 import sweep as S
+    for name, plan in bench.SWEEP_PLANS.items():
+        wl = bench.workload(name)
+        s = S.Solver(wl["eqn"], wl["nx"], wl["ny"], wl["dt"], wl["dx"], wl["tile"], wl["depth"])
+        assert int(s.get("standard_tile")) in plan["standard_tiles"], name
+        for t in plan["standard_tiles"]:
+            s.set("standard_tile", t)
+            assert s.get("standard_tile") == t
+    # --sides: the heat workload on other grid sides, every edge legal there
+    wl = bench.workload("heat16384")
+    for n in bench.HEAT_SIDE_STEPS:
+        w = bench.side_workload(wl, n)
+        assert w["state"].shape == (n, n) and w["nsteps"] == bench.HEAT_SIDE_STEPS[n]
+        s = S.Solver("heat", n, n, w["dt"], w["dx"], w["tile"], w["depth"])
+        assert abs(s.get("r") - 0.1) < 1e-15
+        for t in bench.SWEEP_PLANS["heat16384"]["standard_tiles"]:
+            s.set("standard_tile", t)

@@ -98,9 +98,9 @@ def test_heat_swept_bit_identical(torch_cuda, oracle_lib, nx, ny, tile, nsteps):
 @pytest.mark.parametrize("depth", [14, 30])
 def test_heat_block64_large_levels(torch_cuda, oracle_lib, nx, ny, depth):
     """Block 64.  From 2^20 cells heat runs the wide swept kernels (levels
-    of at least four cells per thread take two neighbouring cells per
-    thread, smaller ones one) and the paired Standard step; below, the
-    one-cell kernels.  Swept and Standard match the oracle bit for bit."""
+    of at least 16 cells per thread take two neighbouring cells per thread,
+    smaller ones one) and the paired Standard step; below, the one-cell
+    kernels.  Swept and Standard match the oracle bit for bit."""
     from paper_2105_10332_b300 import sweep as S
     s, dt, dx = heat_solver(S, nx, ny, 64, depth)
     u0 = W.heat_modes(nx, ny, seed=depth)
@@ -126,12 +126,43 @@ def test_heat_wide_kernels_in_bands(torch_cuda, oracle_lib, cluster, passes):
     assert np.array_equal(got, ref), relerr(got, ref)
 
 
-def test_heat_standard_paired_step_1024(torch_cuda, oracle_lib):
-    """From 2^20 cells the Standard heat step takes two cells per thread:
-    1024^2 against the oracle, bit for bit."""
+@pytest.mark.parametrize("n,tile,depth", [(1036, 14, 6), (1026, 18, 8)])
+def test_heat_wide_kernels_odd_half_edges(torch_cuda, oracle_lib, n, tile, depth):
+    """Above 2^20 cells with block edges whose half is odd: the shifted
+    windows start on odd columns, so a level's pairs start on either parity
+    of column; the Standard edge is the smallest even divisor (14, 18).
+    Swept and Standard against the oracle, bit for bit."""
     from paper_2105_10332_b300 import sweep as S
-    s, dt, dx = heat_solver(S, 1024, 1024, 32, 14)
-    u0 = W.heat_modes(1024, 1024, seed=11)
+    s, dt, dx = heat_solver(S, n, n, tile, depth)
+    u0 = W.heat_modes(n, n, seed=tile)
+    ref = oracle_lib.heat_run(u0, 13, dt, dx)
+    for method in ("run_swept", "run_standard"):
+        got = gpu_run(torch_cuda, s, u0, 13, method)
+        assert np.array_equal(got, ref), (method, relerr(got, ref))
+
+
+def test_heat_wide_kernels_pair_levels(torch_cuda, oracle_lib):
+    """Block 96 on 1056^2: the Up-Pyramid's and the Octahedron's largest
+    levels hold at least 16 cells per thread, so the wide kernels take their
+    two-cells-per-thread branch there (with block 64 no level is that
+    large).  50 steps (two swept cycles of depth 46) against the oracle."""
+    from paper_2105_10332_b300 import sweep as S
+    s, dt, dx = heat_solver(S, 1056, 1056, 96, 46)
+    u0 = W.heat_modes(1056, 1056, seed=96)
+    ref = oracle_lib.heat_run(u0, 50, dt, dx)
+    got = gpu_run(torch_cuda, s, u0, 50, "run_swept")
+    assert np.array_equal(got, ref), relerr(got, ref)
+
+
+@pytest.mark.parametrize("n,edge", [(1024, 32), (2048, 64)])
+def test_heat_standard_paired_step(torch_cuda, oracle_lib, n, edge):
+    """From 2^20 cells the Standard heat step takes two cells per thread,
+    on 64-wide blocks with 512 threads: the default edges at 1024^2 and
+    2048^2 against the oracle, bit for bit."""
+    from paper_2105_10332_b300 import sweep as S
+    s, dt, dx = heat_solver(S, n, n, 32, 14)
+    assert s.get("standard_tile") == edge
+    u0 = W.heat_modes(n, n, seed=11)
     ref = oracle_lib.heat_run(u0, 9, dt, dx)
     got = gpu_run(torch_cuda, s, u0, 9, "run_standard")
     assert np.array_equal(got, ref), relerr(got, ref)
