@@ -303,16 +303,19 @@ int swept_c(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
     return standard_levels<EQ>(h, p, L - done, st);
 }
 
-// Heat on a grid of at least 2^20 cells runs the WIDE swept kernels
-// (Stage<Heat>::run_wide: levels of at least 16 cells per thread in pairs;
-// heat 16384^2, block 64: 49.2 -> 51.9 Gcell-steps/s).  Smaller grids run
-// the one-cell kernels, which the same compiled-in choice slows by ~3 %
-// (heat 64^2).
+// Heat on a grid of at least 2^16 cells runs the WIDE swept kernels
+// (Stage<Heat>::run_wide: levels of at least 16 cells per thread in pairs).
+// Block 64, Gcell-steps/s against the one-cell kernels: heat 16384^2 49.2
+// -> 51.9, 768^2 34.5 -> 35.6, 512^2 17.6 -> 17.9, 256^2 4.42 -> 4.49.
+// Smaller grids run the one-cell kernels, which the wide form slows by
+// 3.5 % at heat 64^2 (0.597 -> 0.576).
+constexpr int64_t kSweptWideCells = int64_t(1) << 16;
+
 template <class EQ, int C, int CB>
 int swept_w(const sweep_s *h, Params p, int64_t nlevels, cudaStream_t st)
 {
     if constexpr (std::is_same<EQ, Heat>::value)
-        if (h->nx * h->ny >= kStdPairsCells) return swept_c<EQ, C, CB, true>(h, p, nlevels, st);
+        if (h->nx * h->ny >= kSweptWideCells) return swept_c<EQ, C, CB, true>(h, p, nlevels, st);
     return swept_c<EQ, C, CB, false>(h, p, nlevels, st);
 }
 
